@@ -1,0 +1,44 @@
+"""Pins for the oracle's GMRES (Sec. 3.2)."""
+import numpy as np
+
+from oracle.gmres import gmres
+
+
+def test_matches_dense_solve():
+    rng = np.random.default_rng(0)
+    A = rng.standard_normal((150, 150)) + 20 * np.eye(150)
+    b = rng.standard_normal(150)
+    x, it, res = gmres(lambda v: A @ v, b, tol=1e-12)
+    assert np.linalg.norm(A @ x - b) / np.linalg.norm(b) < 1e-11
+    assert abs(res - np.linalg.norm(A @ x - b) / np.linalg.norm(b)) < 1e-10
+    assert np.allclose(x, np.linalg.solve(A, b), rtol=1e-9)
+
+
+def test_iterations_equal_distinct_eigenvalues():
+    # Krylov space of a diagonalisable matrix with k distinct eigenvalues has dim k
+    rng = np.random.default_rng(1)
+    Q, _ = np.linalg.qr(rng.standard_normal((60, 60)))
+    ev = np.repeat([1.0, 2.0, 5.0, 7.0, 11.0], 12)
+    A = Q @ np.diag(ev) @ Q.T
+    b = rng.standard_normal(60)
+    x, it, res = gmres(lambda v: A @ v, b, tol=1e-12)
+    assert it == 5
+    assert np.linalg.norm(A @ x - b) / np.linalg.norm(b) < 1e-10
+
+
+def test_right_preconditioner_exact_inverse_converges_in_one():
+    rng = np.random.default_rng(2)
+    A = rng.standard_normal((80, 80)) + 10 * np.eye(80)
+    Ai = np.linalg.inv(A)
+    b = rng.standard_normal(80)
+    x, it, res = gmres(lambda v: A @ v, b, precond=lambda v: Ai @ v, tol=1e-10)
+    assert it == 1
+    assert np.allclose(A @ x, b, atol=1e-9)
+
+
+def test_max_iterations_reported():
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((100, 100))
+    b = rng.standard_normal(100)
+    x, it, res = gmres(lambda v: A @ v, b, tol=1e-14, maxit=7)
+    assert it == 7 and res > 1e-14

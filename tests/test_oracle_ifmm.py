@@ -1,0 +1,136 @@
+"""Pins for the IFMM oracle (Sec. 2.2-2.4, Algorithms 1-3, Appendix C)."""
+import numpy as np
+import pytest
+
+from oracle.h2 import H2
+from oracle.ifmm import IFMM, schur_complement
+from workloads import Kernel, K_GAUSSIAN, K_INV_R, K_PAPER_D, small_cube
+
+
+def setup(N, seed, n, leaf, dim=3, kernel=None):
+    w = small_cube(N, seed, cheb_n=n, leaf_max=leaf, dim=dim, kernel=kernel)
+    h = H2(w.points, w.kernel.kind, w.kernel.param, w.kernel.diag, n, leaf)
+    return w, h
+
+
+def dense_solution(h, b):
+    A = h.dense_blockwise()
+    p = h.tree.perm
+    xt = np.linalg.solve(A, b[p])
+    x = np.empty_like(xt)
+    x[p] = xt
+    return x
+
+
+@pytest.mark.parametrize("N,n,leaf,dim,kernel", [
+    (600, 3, 16, 3, None),                                  # L = 2 (leaves are the top level)
+    (1500, 2, 12, 3, Kernel(K_INV_R, 0.0, 3000.0)),        # L = 3: one merge
+    (900, 3, 10, 2, Kernel(K_GAUSSIAN, 0.15, 1.01)),       # quadtree, L = 3
+    (700, 2, 6, 2, Kernel(K_PAPER_D, 0.05, 1.0)),         # paper kernel, L = 4
+])
+def test_tau_zero_is_exact_block_lu(N, n, leaf, dim, kernel):
+    """With compression disabled the elimination is an exact block LU of E, so
+    the IFMM solve equals the dense solve of A_n (Sec. 2.1-2.2)."""
+    w, h = setup(N, 21, n, leaf, dim, kernel)
+    f = IFMM(h, 0.0, tau=0.0)
+    b = np.random.default_rng(1).standard_normal(N)
+    x = dense_solution(h, b)
+    A = h.dense_blockwise()
+    kappa = np.linalg.cond(A)
+    assert np.linalg.norm(f.solve(b) - x) / np.linalg.norm(x) < 1e-14 * kappa * 50
+
+
+def test_error_tracks_eps():
+    """Sec. 2.4: the retained rank follows eps; the solve error falls with it."""
+    N = 1200
+    w, h = setup(N, 7, 4, 24, 3, Kernel(K_INV_R, 0.0, 4.0 * N))
+    b = np.random.default_rng(1).standard_normal(N)
+    x = dense_solution(h, b)
+    errs, s0 = [], None
+    for eps in (1e-2, 1e-4, 1e-6, 1e-8):
+        f = IFMM(h, eps, sigma0=s0)
+        s0 = f.sigma0
+        errs.append(np.linalg.norm(f.solve(b) - x) / np.linalg.norm(x))
+        assert errs[-1] < 10 * eps
+    assert all(b < a for a, b in zip(errs, errs[1:]))
+
+
+def test_ranks_bounded_and_multi_rhs():
+    w, h = setup(1500, 3, 3, 16)
+    f = IFMM(h, 1e-5)
+    leaf = h.tree.levels[h.L]
+    for i in range(leaf.nb):
+        assert f.rank_log[(h.L, i)] <= leaf.pt_end[i] - leaf.pt_begin[i]
+        assert f.rank_log[(h.L, i)] <= 27
+    B = np.random.default_rng(2).standard_normal((1500, 3))
+    X = f.solve(B)
+    for c in range(3):
+        assert np.allclose(X[:, c], f.solve(B[:, c]), rtol=1e-12, atol=1e-12)
+
+
+def test_dense_mode_for_tiny_n():
+    w, h = setup(40, 2, 3, 64)
+    assert h.tree.dense
+    f = IFMM(h, 1e-6)
+    b = np.random.default_rng(0).standard_normal(40)
+    assert np.allclose(f.solve(b), np.linalg.solve(h.dense_exact(), b), rtol=1e-12)
+
+
+def test_sigma0_is_the_largest_singular_value_of_E():
+    w, h = setup(300, 2, 2, 10, 3, Kernel(K_INV_R, 0.0, 600.0))
+    from oracle.ifmm import sigma0_power
+    s, it = sigma0_power(h)
+    E = h.extended_dense()
+    assert abs(s - np.linalg.svd(E, compute_uv=False)[0]) <= 1e-5 * s
+
+
+def _appendix_c():
+    rng = np.random.default_rng(5)
+    m, r = 7, 3
+    A00 = rng.standard_normal((m, m)) + 6 * np.eye(m)
+    A11 = rng.standard_normal((m, m)) + 6 * np.eye(m)
+    U0, U1, V0, V1 = (rng.standard_normal((m, r)) for _ in range(4))
+    Z = np.zeros
+    I = np.eye(r)
+    E = np.block([[A00, Z((m, m)), U0, Z((m, r))],
+                  [Z((m, m)), A11, Z((m, r)), U1],
+                  [V0.T, Z((r, m)), Z((r, r)), -I],
+                  [Z((r, m)), V1.T, -I, Z((r, r))]])
+    blocks = [slice(0, m), slice(m, 2 * m), slice(2 * m, 2 * m + r), slice(2 * m + r, 2 * m + 2 * r)]
+    return E, blocks, (A00, A11, U0, U1, V0, V1)
+
+
+def _eliminate(E, blocks, piv):
+    keep = [b for k, b in enumerate(blocks) if k not in piv]
+    P = np.concatenate([np.arange(blocks[k].start, blocks[k].stop) for k in piv])
+    R = np.concatenate([np.arange(b.start, b.stop) for b in keep])
+    _, S = schur_complement(E[np.ix_(P, P)], E[np.ix_(P, R)], E[np.ix_(R, P)])
+    return E[np.ix_(R, R)] - S
+
+
+def test_appendix_c_level_by_level_closed_form():
+    """Appendix C: eliminating A00 then A11 leaves
+    [[-V0^T A00^-1 U0, -I], [-I, -V1^T A11^-1 U1]]."""
+    E, blocks, (A00, A11, U0, U1, V0, V1) = _appendix_c()
+    rest = _eliminate(E, blocks, [0, 1])
+    r = U0.shape[1]
+    expect = np.block([[-V0.T @ np.linalg.solve(A00, U0), -np.eye(r)],
+                       [-np.eye(r), -V1.T @ np.linalg.solve(A11, U1)]])
+    assert np.allclose(rest, expect, atol=1e-12)
+
+
+def test_appendix_c_depth_first_closed_form():
+    """Appendix C: eliminating A00, then the two auxiliary pivots, leaves the
+    block-LU Schur complement A11 - U1 V0^T A00^-1 U0 V1^T; the intermediate
+    after A00 is the printed 3x3 block matrix."""
+    E, blocks, (A00, A11, U0, U1, V0, V1) = _appendix_c()
+    m, r = A00.shape[0], U0.shape[1]
+    mid = _eliminate(E, blocks, [0])
+    Z = np.zeros
+    expect_mid = np.block([[A11, Z((m, r)), U1],
+                           [Z((r, m)), -V0.T @ np.linalg.solve(A00, U0), -np.eye(r)],
+                           [V1.T, -np.eye(r), Z((r, r))]])
+    assert np.allclose(mid, expect_mid, atol=1e-12)
+    last = _eliminate(E, blocks, [0, 2, 3])
+    expect = A11 - U1 @ V0.T @ np.linalg.solve(A00, U0) @ V1.T
+    assert np.allclose(last, expect, atol=1e-11)
