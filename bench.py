@@ -1,0 +1,377 @@
+#!/usr/bin/env python3
+"""Benchmark of the IFMM hot path on one GB300 (or N independent replicas).
+
+Workload (default ``c2``): N = 65,536 points uniform in the unit cube,
+A_ij = 1/|x_i - x_j|, A_ii = 2 N^(1/3), leaves <= 64 points, Chebyshev 4x4x4,
+eps = 1e-8, one standard-normal right-hand side, FP64 GMRES to a relative
+residual of 1e-10 with the FMM matvec and the IFMM as right preconditioner.
+
+A step is one pass of the whole path over the synthetic input already resident
+in device memory: tree + lists + colours, operators, sigma_0, weighted bases,
+elimination of every level, top LU, then GMRES (solve sweeps + FMM matvecs).
+``value`` is solves/s (right-hand sides taken to 1e-10 per second of step).
+``e2e`` repeats the step through the C-ABI host-buffer entry points
+(points and b from host memory, x back to host memory).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs its own replica (weak scaling, no collective on
+the data path); rank 0 prints one JSON line.  ``--impl reference`` times the
+CPU oracle on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "IFMM-GMRES solves/s & p50/p99 latency to 1e-10 residual; factor s vs plain FP64"
+UNIT = "solves/s"
+SAMPLE_N = 4096       # oracle sample: same recipe as the workload at reduced N
+FP64_PEAK_TFLOPS = 1.25  # GB300 FP64 (nominal, from the platform recipe; no measured figure)
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=2)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", choices=["c1", "c2"], default="c2")
+    p.add_argument("--schur", choices=["fp64", "tf32"], default="fp64")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def workload(name):
+    import workloads
+    return workloads.c1() if name == "c1" else workloads.c2()
+
+
+def describe(w):
+    return (f"{w.name}: N={w.N} uniform in the unit cube, A_ij=1/r, A_ii=2N^(1/3), "
+            f"leaves<={w.leaf_max}, Chebyshev {w.cheb_n}^3, eps={w.eps:g}, {w.nrhs} RHS, "
+            "FMM matvec, right-preconditioned GMRES to 1e-10")
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.device)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded sample (baseline / reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample_step(w_full):
+    """One oracle pass (tree, operators, sigma_0, factor, GMRES) on the workload's
+    recipe at N = SAMPLE_N; returns (seconds, iterations, true residual)."""
+    import numpy as np
+
+    import workloads
+    from oracle.gmres import gmres
+    from oracle.h2 import H2
+    from oracle.ifmm import IFMM
+    w = workloads.inv_r_cube(SAMPLE_N, w_full.seed, "sample", w_full.cheb_n, w_full.leaf_max,
+                             w_full.eps)
+    b = w.rhs(1)[:, 0]
+    t0 = time.perf_counter()
+    h2 = H2(w.points, w.kernel.kind, w.kernel.param, w.kernel.diag, w.cheb_n, w.leaf_max)
+    f = IFMM(h2, w.eps)
+    p = h2.tree.perm
+
+    def mv(v):
+        out = np.empty_like(v)
+        out[p] = h2.matvec(v[p])
+        return out
+
+    x, it, _ = gmres(mv, b, f.solve, 1e-10, 500)
+    dt = time.perf_counter() - t0
+    res = float(np.linalg.norm(mv(x) - b) / np.linalg.norm(b))
+    return dt, it, res
+
+
+def sample_text(w):
+    return (f"the oracle's full pass (tree, operators, sigma_0, factor, GMRES) on the same recipe "
+            f"at N={SAMPLE_N} (seed {w.seed}); solves/s scaled to N={w.N} by the O(N) cost of "
+            f"the method (x{SAMPLE_N}/{w.N})")
+
+
+def cpu_baseline(w):
+    dt, it, res = oracle_sample_step(w)
+    return {"value": (1.0 / dt) * (SAMPLE_N / w.N), "unit": UNIT, "cores": os.cpu_count(),
+            "kind": "oracle", "sample": sample_text(w), "sample_seconds": round(dt, 2),
+            "sample_iters": it, "sample_true_residual": res}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = workload(args.workload)
+    for _ in range(args.warmup):
+        oracle_sample_step(w)
+    times, its = [], []
+    for _ in range(args.steps):
+        dt, it, res = oracle_sample_step(w)
+        times.append(dt)
+        its.append(it)
+    total = sum(times)
+    value = args.steps * (SAMPLE_N / w.N) / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps * (w.N / SAMPLE_N),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": describe(w)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(),
+                             "kind": "oracle", "sample": sample_text(w)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "iterations": its}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1508_01835_gb300 as ifmm
+    from paper_1508_01835_gb300 import build
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if not os.path.exists(ifmm.LIB_PATH):
+        build.build()
+    w = workload(args.workload)
+    dev = torch.device("cuda", local)
+    pts_h = np.ascontiguousarray(w.points)
+    b_h = np.ascontiguousarray(w.rhs(w.nrhs).T)        # (nrhs, N)
+    pts = torch.tensor(pts_h, device=dev)
+    b = torch.tensor(b_h, device=dev)
+    x = torch.empty_like(b)
+    ctx = ifmm.ifmm_ctx_create(local)
+    schur = ifmm.P_TF32 if args.schur == "tf32" else ifmm.P_FP64
+    opt = ifmm.make_options(dim=w.dim, cheb_n=w.cheb_n, leaf_max=w.leaf_max, eps=w.eps,
+                            schur=schur)
+    kern = ifmm.Kernel(w.kernel.kind, w.kernel.param, w.kernel.diag)
+    stream = torch.cuda.current_stream()
+
+    def step(host=False):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(stream)
+        if host:
+            sys_h = ifmm.ifmm_system_create_host(ctx, pts_h, kern, opt)
+        else:
+            sys_h = ifmm.ifmm_system_create(ctx, pts, kern, opt)
+        fac = ifmm.ifmm_factor(ctx, sys_h)
+        ev[1].record(stream)
+        if host:
+            xh = np.empty_like(b_h)
+            reps = ifmm.gmres_solve_host(ctx, sys_h, fac, ifmm.MV_FMM, b_h, xh, 1e-10, 500)
+        else:
+            reps = ifmm.gmres_solve(ctx, sys_h, fac, ifmm.MV_FMM, b, x, w.N, 1e-10, 500)
+        ev[2].record(stream)
+        info = ifmm.ifmm_factor_get_info(fac)
+        ifmm.ifmm_factor_destroy(fac)
+        ifmm.ifmm_system_destroy(sys_h)
+        return ev, reps, info
+
+    for _ in range(args.warmup):
+        step()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    ifmm.ifmm_profile_start(ctx)
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    recs = [step() for _ in range(args.steps)]
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    stats = ifmm.ifmm_profile_stop(ctx)
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+    ms = t_start.elapsed_time(t_end)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    step_ms = [ev[0].elapsed_time(ev[2]) for ev, _, _ in recs]
+    factor_ms = [ev[0].elapsed_time(ev[1]) for ev, _, _ in recs]
+    solve_ms = [ev[1].elapsed_time(ev[2]) for ev, _, _ in recs]
+    reps = [r for _, rr, _ in recs for r in rr]
+    info = recs[-1][2]
+    nsolves = args.steps * w.nrhs * world
+    value = nsolves / (ms / 1e3)
+    ok = all(r.status == 0 and r.true_rel_residual <= 1e-10 for r in reps)
+
+    # end to end through the host-buffer entry points
+    e2e = None
+    if not args.no_e2e:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step(host=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        e2e = {"value": args.steps * w.nrhs / dt, "unit": UNIT,
+               "h2d_bytes_per_step": int(pts_h.nbytes + b_h.nbytes),
+               "d2h_bytes_per_step": int(b_h.nbytes)}
+
+    # roofline of the dominant kernel, from the library's own event timings
+    kern_stats = {k: v for k, v in stats.items() if not k.startswith("(")}
+    dom = max(kern_stats.items(), key=lambda kv: kv[1][1]) if kern_stats else None
+    roofline = None
+    if dom:
+        name, (launches, secs, flops, nbytes) = dom
+        if name == "k_spmm":
+            peak = _measured_peaks().get("hbm_gbs")
+            achieved = nbytes / secs / 1e9
+            roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak if peak else None,
+                        "traffic": _traffic(name), "kernel": name, "peak_source": "measured"}
+        else:
+            achieved = flops / secs / 1e12
+            roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                        "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                        "traffic": _traffic(name), "kernel": name,
+                        "peak_source": "FP64 nominal 1.25 TFLOP/s (no measured FP64 figure)",
+                        "launches": launches, "share_of_step": secs / (ms / 1e3)}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": describe(w), "schur": args.schur,
+                   "l2": "inputs larger than L2 (factor working set > 129 MB)",
+                   "replicas": "independent per GPU"},
+        "latency_ms": {"p50": _pct(step_ms, 50), "p99": _pct(step_ms, 99)},
+        "solve_latency_ms": {"p50": _pct(solve_ms, 50), "p99": _pct(solve_ms, 99)},
+        "factor_s": statistics.median(factor_ms) / 1e3,
+        "gmres_iterations": [r.iters for r in reps],
+        "true_rel_residual": max(r.true_rel_residual for r in reps),
+        "converged": ok,
+        "factor_phases_s": {"init": info.seconds_init, "sigma0": info.seconds_sigma0,
+                            "elim": info.seconds_elim, "top": info.seconds_top},
+        "ranks": {str(l): [info.max_rank[l], round(info.avg_rank[l], 1)]
+                  for l in range(2, info.levels + 1)},
+        "clocks": clk, "e2e": e2e, "roofline": roofline,
+        "gpu_launches": int(stats.get("(all launches)", (0,))[0]),
+        "kernels": {k: {"launches": v[0], "s": round(v[1], 4)} for k, v in kern_stats.items()},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ifmm.ifmm_ctx_destroy(ctx)
+    if dist:
+        dist.destroy_process_group()
+
+
+def _pct(v, q):
+    s = sorted(v)
+    if not s:
+        return None
+    k = min(len(s) - 1, max(0, int(math.ceil(q / 100.0 * len(s))) - 1))
+    return s[k]
+
+
+def _measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {"hbm_gbs": 6800.0}
+
+
+def _traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it covers `kernel`."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            return json.load(f).get(kernel)
+    except (OSError, ValueError):
+        return None
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,206 @@
+/*
+ * ifmm.h -- C ABI of the GB300 inverse fast multipole method (IFMM) library.
+ *
+ * The library factorises the H^2 (Chebyshev black-box FMM) representation
+ * A_n of a dense kernel matrix a_ij = K(|r_i - r_j|) (Coulier, Pouransari,
+ * Darve, "The inverse fast multipole method", Sec. 2) and uses the
+ * factorisation as a right preconditioner for FP64 GMRES whose products are
+ * FMM (or direct) matvecs (Sec. 3.2).
+ *
+ * Conventions that hold for every call:
+ *  - every function returns ifmm_status; no C++ exception crosses the ABI;
+ *    ifmm_last_error(ctx) gives a one-line description of the last failure;
+ *  - vectors are FP64, column-major (N rows, nrhs columns, leading dimension
+ *    ld >= N) in USER point order; the library permutes internally;
+ *  - "device" pointers are CUDA device memory of the context's device;
+ *    "host" pointers are ordinary host memory;
+ *  - calls run on the caller's CUDA stream (ifmm_stream is a cudaStream_t;
+ *    NULL = the legacy default stream); a call returns after its work is
+ *    queued unless the description says it synchronises;
+ *  - handles are opaque, owned by the caller, freed by their *_destroy;
+ *    a factorisation keeps a pointer to its system: destroy it first;
+ *  - invalid arguments return IFMM_ERR_INVALID_ARG and change nothing.
+ */
+#ifndef IFMM_H
+#define IFMM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* ifmm_stream; /* same type as cudaStream_t */
+
+typedef struct ifmm_ctx ifmm_ctx;
+typedef struct ifmm_system ifmm_system;
+typedef struct ifmm_factorization ifmm_factorization;
+
+typedef enum {
+  IFMM_OK = 0,
+  IFMM_ERR_INVALID_ARG = 1,
+  IFMM_ERR_OOM = 2,
+  IFMM_ERR_CUDA = 3,
+  IFMM_ERR_SINGULAR_PIVOT = 4, /* a pivot block E(P,P) had a pivot <= 1e-14 max|E(P,P)| */
+  IFMM_ERR_NOT_CONVERGED = 5,  /* GMRES reached maxit above tol (report still filled) */
+  IFMM_ERR_TIMEOUT = 6,
+  IFMM_ERR_BUDGET = 7,
+  IFMM_ERR_UNSUPPORTED = 8
+} ifmm_status;
+
+/* Kernel of the matrix (Sec. 3.1). */
+typedef enum {
+  IFMM_K_INV_R = 0,    /* 1/r                                  */
+  IFMM_K_GAUSSIAN = 1, /* exp(-r^2 / (2 param^2))              */
+  IFMM_K_PAPER_D = 2   /* Eq. (K_ij): r/d for r < d, d/r else  */
+} ifmm_kernel_kind;
+
+typedef struct {
+  int kind;     /* ifmm_kernel_kind                                           */
+  double param; /* Gaussian sigma, or d of the paper kernel; unused for 1/r    */
+  double diag;  /* A_ii (also used for coincident points); NaN = K(0), which
+                   the 1/r kernel does not have (then NaN is invalid)          */
+} ifmm_kernel;
+
+/* Input precision of the Schur-update products (Sec. 2.2, Algorithm 2). */
+typedef enum { IFMM_P_FP64 = 0, IFMM_P_TF32 = 1, IFMM_P_BF16 = 2 } ifmm_precision;
+
+typedef struct {
+  int dim;             /* 2 or 3                                                    */
+  int cheb_n;          /* Chebyshev nodes per dimension, 1..8 (Sec. 3)             */
+  int leaf_max;        /* leaf boxes hold at most this many points, >= 1           */
+  double eps;          /* rank rule tolerance of Eq. (methods_SVD_rank_spectralnorm);
+                          0 disables compression (exact block LU of E)             */
+  int schur;           /* ifmm_precision of the Schur products                      */
+  double tau_override; /* > 0: use this absolute threshold instead of eps*sigma_0   */
+  int rank_cap;        /* >= 1: cap on every box rank; 0 = automatic (2 n^D, or no
+                          cap when eps == 0)                                        */
+  int fmm_n;           /* Chebyshev order of fmm_matvec; 0 = cheb_n                 */
+} ifmm_options;
+
+typedef enum { IFMM_MV_FMM = 0, IFMM_MV_DIRECT = 1 } ifmm_matvec_mode;
+
+typedef struct {
+  int iters;                /* Arnoldi steps taken                                   */
+  double rel_residual;      /* GMRES estimate |g_{k+1}| / ||b||                       */
+  double true_rel_residual; /* ||b - A x|| / ||b|| recomputed with the same matvec    */
+  int status;               /* IFMM_OK or IFMM_ERR_NOT_CONVERGED                      */
+} ifmm_gmres_report;
+
+typedef struct {
+  long long N;
+  int dim;
+  int levels;         /* leaf depth L (0 = no tree: N <= leaf_max, one dense block) */
+  int boxes[32];      /* non-empty boxes per depth 0..L                              */
+  int max_leaf;       /* fullest leaf                                                */
+  double lo[3];       /* root box corner                                             */
+  double edge;        /* root box edge                                               */
+} ifmm_system_info;
+
+typedef struct {
+  double sigma0;        /* sigma_0(E) (NaN when tau_override was used)               */
+  int sigma0_iters;     /* power iterations                                          */
+  double tau;           /* absolute truncation threshold used                        */
+  int levels;           /* leaf depth L                                              */
+  int top_size;         /* order of the top dense system (sum of level-2 ranks)      */
+  int max_rank[32];     /* per depth 2..L: largest rank at elimination               */
+  double avg_rank[32];  /* per depth: mean rank at elimination                       */
+  int rank_capped;      /* number of rank decisions the cap truncated                */
+  int singular_pivots;  /* pivot blocks that triggered the singular-pivot test        */
+  double flops_lu, flops_trsm, flops_schur, flops_lowrank, flops_top;
+  double seconds_init, seconds_sigma0, seconds_elim, seconds_top;
+  long long factor_bytes; /* device bytes held by the factorisation                  */
+} ifmm_factor_info;
+
+/* One row of the launch profile: the library's own launches of one kernel. */
+typedef struct {
+  char name[48];
+  long long launches;
+  double seconds;   /* summed CUDA-event intervals around the launches        */
+  double flops;     /* algorithmic flops of those launches                    */
+  double bytes;     /* algorithmic bytes moved (0 where not counted)          */
+} ifmm_kernel_stat;
+
+/* ---- context ------------------------------------------------------------ */
+/* Select CUDA device `device` and create a context (owns no GPU memory yet). */
+ifmm_status ifmm_ctx_create(int device, ifmm_ctx** out);
+void ifmm_ctx_destroy(ifmm_ctx* ctx);
+const char* ifmm_last_error(const ifmm_ctx* ctx);
+const char* ifmm_status_string(ifmm_status st);
+
+/* ---- system: tree, lists, colours, raw operators (Sec. 2.1, 2.3) ------------ */
+/* pts: device, N x dim row-major, user order; copied.  Builds the uniform tree
+ * (Algorithm 1, line 1), the neighbour / interaction lists and colour classes,
+ * the Chebyshev operators and the near-field blocks.  Synchronises `stream`. */
+ifmm_status ifmm_system_create(ifmm_ctx* ctx, const double* pts, long long N,
+                               const ifmm_kernel* kernel, const ifmm_options* opt,
+                               ifmm_stream stream, ifmm_system** out);
+/* Same, with pts in host memory. */
+ifmm_status ifmm_system_create_host(ifmm_ctx* ctx, const double* pts_host, long long N,
+                                    const ifmm_kernel* kernel, const ifmm_options* opt,
+                                    ifmm_stream stream, ifmm_system** out);
+void ifmm_system_destroy(ifmm_system* sys);
+ifmm_status ifmm_system_get_info(const ifmm_system* sys, ifmm_system_info* info);
+/* perm_host[t] = user index of the t-th point in tree order (N entries). */
+ifmm_status ifmm_system_get_perm(const ifmm_system* sys, long long* perm_host);
+
+/* sigma_0(E), the largest singular value of the extended sparse matrix E
+ * (Sec. 2.4), by power iteration on E^T E with the raw operators: start
+ * vector all ones, stop at relative change <= 1e-6 or 100 iterations.
+ * Synchronises `stream`; the value is cached in the system. */
+ifmm_status ifmm_sigma0(ifmm_ctx* ctx, ifmm_system* sys, ifmm_stream stream, double* sigma0,
+                        int* iters);
+
+/* ---- factorisation (Algorithms 1-3) ---------------------------------------- */
+/* Eliminates levels L..2 colour by colour with fill-in compression and
+ * redirection, then factorises the top dense system.  Synchronises `stream`
+ * (it reads back ranks between colours).  Returns IFMM_ERR_SINGULAR_PIVOT
+ * (with *out still valid) if a pivot block failed the pivot test. */
+ifmm_status ifmm_factor(ifmm_ctx* ctx, ifmm_system* sys, ifmm_stream stream,
+                        ifmm_factorization** out);
+void ifmm_factor_destroy(ifmm_factorization* fac);
+ifmm_status ifmm_factor_get_info(const ifmm_factorization* fac, ifmm_factor_info* info);
+/* Ranks at elimination of the boxes of depth `level` (Morton order), host array
+ * of `capacity` ints; *count receives the number of boxes. */
+ifmm_status ifmm_factor_get_ranks(const ifmm_factorization* fac, int level, int* ranks_host,
+                                  int capacity, int* count);
+/* Device bytes held by the factorisation. */
+ifmm_status ifmm_factor_footprint(const ifmm_factorization* fac, unsigned long long* bytes);
+
+/* ---- solve (substitution phase, Algorithm 1 lines 8-17) ----------------------- */
+/* x = (IFMM factorisation)^-1 b ~= A_n^-1 b.  b, x: device, N x nrhs, ld >= N;
+ * b and x may alias. */
+ifmm_status ifmm_solve(ifmm_ctx* ctx, const ifmm_factorization* fac, const double* b, double* x,
+                       int nrhs, long long ld, ifmm_stream stream);
+
+/* ---- matvec (Sec. 3.2) ------------------------------------------------------- */
+/* y = A_n x (IFMM_MV_FMM, Chebyshev order opt->fmm_n) or y = A x
+ * (IFMM_MV_DIRECT, O(N^2)).  x, y: device, N x nrhs, ld >= N, must not alias. */
+ifmm_status fmm_matvec(ifmm_ctx* ctx, const ifmm_system* sys, int mode, const double* x,
+                       double* y, int nrhs, long long ld, ifmm_stream stream);
+
+/* ---- GMRES (Sec. 3.2) -------------------------------------------------------- */
+/* Non-restarted GMRES, x_0 = 0, CGS2 Arnoldi, Givens rotations, the
+ * factorisation as right preconditioner (fac may be NULL: unpreconditioned).
+ * Each of the nrhs columns is an independent solve.  rep: host array of nrhs
+ * reports.  Synchronises `stream` (reads the residual estimate every step).
+ * Returns IFMM_ERR_NOT_CONVERGED if any column stopped at maxit above tol. */
+ifmm_status gmres_solve(ifmm_ctx* ctx, const ifmm_system* sys, const ifmm_factorization* fac,
+                        int mode, const double* b, double* x, int nrhs, long long ld, double tol,
+                        int maxit, ifmm_gmres_report* rep, ifmm_stream stream);
+/* Same with b, x in host memory (copied to and from the device inside). */
+ifmm_status gmres_solve_host(ifmm_ctx* ctx, const ifmm_system* sys,
+                             const ifmm_factorization* fac, int mode, const double* b_host,
+                             double* x_host, int nrhs, long long ld, double tol, int maxit,
+                             ifmm_gmres_report* rep, ifmm_stream stream);
+
+/* ---- launch profile ------------------------------------------------------ */
+/* Start recording an event pair around each of the library's launches (on
+ * the launching stream); resets the totals.  Process-wide. */
+ifmm_status ifmm_profile_start(ifmm_ctx* ctx);
+/* Synchronise the device, stop recording and return per-kernel totals in
+ * stats (host array of `capacity`); *count receives the number of kernels. */
+ifmm_status ifmm_profile_stop(ifmm_ctx* ctx, ifmm_kernel_stat* stats, int capacity, int* count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IFMM_H */

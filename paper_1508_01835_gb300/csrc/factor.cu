@@ -1,0 +1,743 @@
+// factor.cu -- IFMM elimination (Algorithms 1-3 of the paper) on the GPU.
+//
+// Level by level (l = L .. 2) the driver
+//   1. builds weighted bases for the level (footnote to Eq. U_j_recomp):
+//      left SVD of U_i [K_iq V_q^T]_{q in I_i}, truncated at tau (reading R6);
+//   2. eliminates the level colour by colour (colour = box index mod 3 per
+//      dimension; boxes of one colour have disjoint neighbour lists, so all of
+//      them are eliminated in the same launches):
+//        gather E(P,P), E(P,C), E(R,P) of every box  -> batched LU (FP64)
+//        -> G = E(P,P)^-1 E(P,C) -> S = E(R,P) G (Schur product)
+//        -> scatter -S into neighbour / M2L edges, keep well-separated fill;
+//   3. recompresses the bases of the boxes that received well-separated fill
+//      (Eqs. U_j_recomp, V_j_recomp; aggregated per box, reading R4) and
+//      redirects every edge of those boxes (Algorithm 3, Eq. K_kj_update);
+//   4. merges the level into its parent (Eqs. y_merge - K_merge).
+// The top system for y^(2) is factorised densely.
+#include <chrono>
+#include <memory>
+#include <map>
+#include <set>
+
+#include "factor.cuh"
+
+namespace ifmm {
+
+using Clock = std::chrono::steady_clock;
+static double since(Clock::time_point t) {
+  return std::chrono::duration<double>(Clock::now() - t).count();
+}
+
+static inline GemmTask gm(const double* A, int lda, int tA, const double* B, int ldb, int tB,
+                          double* C, int ldc, int M, int N, int K, double alpha, double beta) {
+  return GemmTask{A, B, C, lda, ldb, ldc, M, N, K, tA, tB, alpha, beta};
+}
+static inline CopyTask cp(const double* src, int lds, double* dst, int ldd, int rows, int cols,
+                          int trans = 0, double alpha = 1.0, double beta = 0.0,
+                          const double* cscale = nullptr, int kind = 0) {
+  return CopyTask{src, dst, cscale, lds, ldd, rows, cols, trans, kind, alpha, beta};
+}
+static inline CopyTask cp_eye(double* dst, int ldd, int n, double alpha) {
+  return CopyTask{nullptr, dst, nullptr, 1, ldd, n, n, 0, 1, alpha, 0.0};
+}
+static inline CopyTask cp_zero(double* dst, int ldd, int rows, int cols) {
+  return CopyTask{nullptr, dst, nullptr, 1, ldd, rows, cols, 0, 2, 0.0, 0.0};
+}
+
+static void run_copies(Arena& ar, const std::vector<CopyTask>& v, cudaStream_t s) {
+  std::vector<CopyTask> keep;
+  keep.reserve(v.size());
+  for (const CopyTask& c : v)
+    if (c.rows > 0 && c.cols > 0) {
+      validate(c);
+      keep.push_back(c);
+    }
+  if (keep.empty()) return;
+  const CopyTask* d = upload(ar, keep, s);
+  launch_copy(d, (int)keep.size(), s);
+}
+
+struct FLevel {
+  int l = 0, nb = 0;
+  std::vector<int> a, r, rcap;
+  std::vector<char> elim;
+  std::vector<double*> X, Y;  // per neighbour slot (ld a_i) / per N u I slot (ld rcap_i)
+  std::vector<double*> U, V, SU, SV, Upar, Vpar;
+  std::vector<double*> Uraw, Vraw;  // raw bases of this level (a_i x nd, ld a_i)
+  Arena mem;
+};
+
+struct Factorizer {
+  ifmm_system* sys;
+  ifmm_factorization* f;
+  cudaStream_t s;
+  const ChebOps& ops;
+  int nd, dim;
+  double tau = 0.0;
+  int cap_global = 0;
+  Arena scratch;
+  int* d_counters = nullptr;  // [0]: rank cap hits
+
+  Factorizer(ifmm_system* sy, ifmm_factorization* fa, cudaStream_t st)
+      : sys(sy), f(fa), s(st), ops(sy->ops_f), nd(sy->ops_f.nd), dim(sy->dim) {}
+
+  double* X(FLevel& st, const LevelTopo& lv, int i, int j) {
+    const int k = lv.nslot(i, j);
+    if (k < 0) throw Error(IFMM_ERR_CUDA, "internal: missing near block");
+    return st.X[k];
+  }
+  double* Y(FLevel& st, const LevelTopo& lv, int i, int j) {
+    const int k = lv.yslot(i, j);
+    if (k < 0) throw Error(IFMM_ERR_CUDA, "internal: missing far block");
+    return st.Y[k];
+  }
+
+  void alloc_level(FLevel& st, const LevelTopo& lv) {
+    st.l = lv.l;
+    st.nb = lv.nb;
+    st.rcap.resize(st.nb);
+    for (int i = 0; i < st.nb; i++) st.rcap[i] = std::min(st.a[i], cap_global);
+    st.r.assign(st.nb, 0);
+    st.elim.assign(st.nb, 0);
+    long long nx = 0, ny = 0, nu = 0, ns = 0, np = 0;
+    for (int i = 0; i < st.nb; i++) {
+      for (int k = lv.nbr_ptr[i]; k < lv.nbr_ptr[i + 1]; k++)
+        nx += (long long)st.a[i] * st.a[lv.nbr[k]];
+      for (int k = lv.yl_ptr[i]; k < lv.yl_ptr[i + 1]; k++)
+        ny += (long long)st.rcap[i] * st.rcap[lv.yl[k]];
+      nu += (long long)st.a[i] * st.rcap[i];
+      ns += st.rcap[i];
+      np += (long long)st.rcap[i] * nd;
+    }
+    double* bx = st.mem.alloc<double>(std::max(nx, 1ll));
+    double* by = st.mem.alloc<double>(std::max(ny, 1ll));
+    CK(cudaMemsetAsync(by, 0, sizeof(double) * std::max(ny, 1ll), s));
+    double* bu = st.mem.alloc<double>(std::max(2 * nu, 1ll));
+    double* bs = st.mem.alloc<double>(std::max(2 * ns, 1ll));
+    double* bp = st.mem.alloc<double>(std::max(2 * np, 1ll));
+    st.X.assign(lv.nbr.size(), nullptr);
+    st.Y.assign(lv.yl.size(), nullptr);
+    st.U.resize(st.nb); st.V.resize(st.nb); st.SU.resize(st.nb); st.SV.resize(st.nb);
+    st.Upar.resize(st.nb); st.Vpar.resize(st.nb);
+    long long ox = 0, oy = 0, ou = 0, os = 0, op = 0;
+    for (int i = 0; i < st.nb; i++) {
+      for (int k = lv.nbr_ptr[i]; k < lv.nbr_ptr[i + 1]; k++) {
+        st.X[k] = bx + ox;
+        ox += (long long)st.a[i] * st.a[lv.nbr[k]];
+      }
+      for (int k = lv.yl_ptr[i]; k < lv.yl_ptr[i + 1]; k++) {
+        st.Y[k] = by + oy;
+        oy += (long long)st.rcap[i] * st.rcap[lv.yl[k]];
+      }
+      st.U[i] = bu + ou;
+      st.V[i] = bu + nu + ou;
+      ou += (long long)st.a[i] * st.rcap[i];
+      st.SU[i] = bs + os;
+      st.SV[i] = bs + ns + os;
+      os += st.rcap[i];
+      st.Upar[i] = bp + op;
+      st.Vpar[i] = bp + np + op;
+      op += (long long)st.rcap[i] * nd;
+    }
+  }
+
+  // sync and read ranks written by rank tasks
+  std::vector<int> read_ints(const int* d, int n) {
+    std::vector<int> h(n);
+    if (n > 0) CK(cudaMemcpyAsync(h.data(), d, n * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return h;
+  }
+
+  // -------------------------------------------------------------------------
+  // weighted initial bases of a level (footnote to Eq. U_j_recomp, reading R6)
+  // -------------------------------------------------------------------------
+  void init_basis(FLevel& st, const LevelTopo& lv) {
+    const int nb = st.nb;
+    const double s0 = std::isnan(sys->sigma0) ? 1.0 : sys->sigma0;
+    // process boxes in batches that keep the SVD inputs below ~2 GiB
+    std::vector<double*> WU(nb), WV(nb), sU(nb), sV(nb);
+    Arena keep;  // W and sigma of all boxes until ranks are known
+    for (int i = 0; i < nb; i++) {
+      const int a = st.a[i];
+      WU[i] = keep.alloc<double>((size_t)a * a);
+      WV[i] = keep.alloc<double>((size_t)a * a);
+      sU[i] = keep.alloc<double>(a);
+      sV[i] = keep.alloc<double>(a);
+    }
+    int* d_r = keep.alloc<int>(nb);
+    int i0 = 0;
+    while (i0 < nb) {
+      scratch.reset();
+      long long budget = 0;
+      int i1 = i0;
+      while (i1 < nb) {
+        long long w = 0;
+        for (int k = lv.far_ptr[i1]; k < lv.far_ptr[i1 + 1]; k++) w += st.a[lv.far[k]];
+        if (w == 0) w = nd;
+        const long long need = 2 * ((long long)st.a[i1] * w + (long long)nd * w);
+        if (i1 > i0 && budget + need > (256ll << 20)) break;
+        budget += need;
+        i1++;
+      }
+      std::vector<GemmTask> g1, g2;
+      std::vector<CopyTask> cps;
+      std::vector<SvdTask> svd;
+      for (int i = i0; i < i1; i++) {
+        const int a = st.a[i];
+        long long w = 0;
+        for (int k = lv.far_ptr[i]; k < lv.far_ptr[i + 1]; k++) w += st.a[lv.far[k]];
+        double* MU;
+        double* MV;
+        int wcols;
+        if (w == 0) {
+          // empty interaction list: weight the raw basis by sigma_0 (reading R6)
+          wcols = nd;
+          MU = scratch.alloc<double>((size_t)a * nd);
+          MV = scratch.alloc<double>((size_t)a * nd);
+          cps.push_back(cp(st.Uraw[i], a, MU, a, a, nd, 0, s0));
+          cps.push_back(cp(st.Vraw[i], a, MV, a, a, nd, 0, s0));
+        } else {
+          wcols = (int)w;
+          double* BU = scratch.alloc<double>((size_t)nd * w);
+          double* BV = scratch.alloc<double>((size_t)nd * w);
+          MU = scratch.alloc<double>((size_t)a * w);
+          MV = scratch.alloc<double>((size_t)a * w);
+          long long off = 0;
+          for (int k = lv.far_ptr[i]; k < lv.far_ptr[i + 1]; k++) {
+            const int q = lv.far[k];
+            const int aq = st.a[q];
+            const double* Kiq = ops.m2l[lv.l] + (size_t)lv.m2l_offset(i, q, dim) * nd * nd;
+            const double* Kqi = ops.m2l[lv.l] + (size_t)lv.m2l_offset(q, i, dim) * nd * nd;
+            // BU[:, off] = K_iq V_q^T ; BV[:, off] = K_qi^T U_q^T
+            g1.push_back(gm(Kiq, nd, 0, st.Vraw[q], aq, 1, BU + off * nd, nd, nd, aq, nd, 1.0, 0.0));
+            g1.push_back(gm(Kqi, nd, 1, st.Uraw[q], aq, 1, BV + off * nd, nd, nd, aq, nd, 1.0, 0.0));
+            off += aq;
+          }
+          g2.push_back(gm(st.Uraw[i], a, 0, BU, nd, 0, MU, a, a, (int)w, nd, 1.0, 0.0));
+          g2.push_back(gm(st.Vraw[i], a, 0, BV, nd, 0, MV, a, a, (int)w, nd, 1.0, 0.0));
+        }
+        double* wk1 = a > 128 ? scratch.alloc<double>((size_t)a * a + (size_t)a * 32) : nullptr;
+        double* wk2 = a > 128 ? scratch.alloc<double>((size_t)a * a + (size_t)a * 32) : nullptr;
+        svd.push_back({MU, a, a, wcols, WU[i], sU[i], wk1});
+        svd.push_back({MV, a, a, wcols, WV[i], sV[i], wk2});
+        f->info.flops_lowrank += 4.0 * a * a * (double)wcols * 2;
+      }
+      run_copies(scratch, cps, s);
+      run_gemms(scratch, g1, s);
+      run_gemms(scratch, g2, s);
+      run_svd_left(scratch, svd, s);
+      std::vector<RankTask> rt;
+      for (int i = i0; i < i1; i++) {
+        const int k = std::min(st.a[i], nd);
+        rt.push_back({sU[i], sV[i], k, std::min(k, st.rcap[i]), d_r + i, d_counters});
+      }
+      const RankTask* drt = upload(scratch, rt, s);
+      launch_rank(drt, (int)rt.size(), tau, s);
+      CK(cudaStreamSynchronize(s));
+      i0 = i1;
+    }
+    std::vector<int> r = read_ints(d_r, nb);
+    scratch.reset();
+    // r_i = W_r^T U_raw, t_i = W_r^T V_raw; new bases; M2L edges; parent transfers
+    std::vector<double*> rt(nb), tt(nb);
+    std::vector<GemmTask> g, g2;
+    std::vector<CopyTask> cps;
+    for (int i = 0; i < nb; i++) {
+      const int a = st.a[i];
+      st.r[i] = r[i];
+      rt[i] = scratch.alloc<double>((size_t)std::max(r[i], 1) * nd);
+      tt[i] = scratch.alloc<double>((size_t)std::max(r[i], 1) * nd);
+      g.push_back(gm(WU[i], a, 1, st.Uraw[i], a, 0, rt[i], std::max(r[i], 1), r[i], nd, a, 1.0, 0.0));
+      g.push_back(gm(WV[i], a, 1, st.Vraw[i], a, 0, tt[i], std::max(r[i], 1), r[i], nd, a, 1.0, 0.0));
+      cps.push_back(cp(WU[i], a, st.U[i], a, a, r[i]));
+      cps.push_back(cp(WV[i], a, st.V[i], a, a, r[i]));
+      cps.push_back(cp(sU[i], 1, st.SU[i], 1, r[i], 1));
+      cps.push_back(cp(sV[i], 1, st.SV[i], 1, r[i], 1));
+    }
+    run_gemms(scratch, g, s);
+    run_copies(scratch, cps, s);
+    g.clear();
+    for (int i = 0; i < nb; i++) {
+      const int ri = st.r[i];
+      const int ldr = std::max(ri, 1);
+      for (int k = lv.far_ptr[i]; k < lv.far_ptr[i + 1]; k++) {
+        const int q = lv.far[k];
+        const double* Kiq = ops.m2l[lv.l] + (size_t)lv.m2l_offset(i, q, dim) * nd * nd;
+        double* T1 = scratch.alloc<double>((size_t)ldr * nd);
+        g.push_back(gm(rt[i], ldr, 0, Kiq, nd, 0, T1, ldr, ri, nd, nd, 1.0, 0.0));
+        g2.push_back(gm(T1, ldr, 0, tt[q], std::max(st.r[q], 1), 1, Y(st, lv, i, q), st.rcap[i],
+                        ri, st.r[q], nd, 1.0, 0.0));
+      }
+      if (lv.l > 2) {
+        const double* Tc = ops.transfer + (size_t)lv.child_pos(i, dim) * nd * nd;
+        g.push_back(gm(rt[i], ldr, 0, Tc, nd, 0, st.Upar[i], st.rcap[i], ri, nd, nd, 1.0, 0.0));
+        g.push_back(gm(tt[i], ldr, 0, Tc, nd, 0, st.Vpar[i], st.rcap[i], ri, nd, nd, 1.0, 0.0));
+      }
+    }
+    run_gemms(scratch, g, s);
+    run_gemms(scratch, g2, s);
+    CK(cudaStreamSynchronize(s));
+    scratch.reset();
+  }
+
+  // -------------------------------------------------------------------------
+  // elimination of one colour class (Algorithm 2, aggregated reading R4)
+  // -------------------------------------------------------------------------
+  void eliminate_colour(FLevel& st, const LevelTopo& lv, const std::vector<int>& boxes) {
+    scratch.reset();
+    const int nbx = (int)boxes.size();
+    std::vector<FRec> recs(nbx);
+    std::vector<double*> S(nbx);
+    std::vector<CopyTask> cps;
+    std::vector<LuTask> lus;
+    std::vector<RsTask> rss;
+    std::vector<GemmTask> gs;
+    for (int b = 0; b < nbx; b++) {
+      const int i = boxes[b];
+      FRec& R = recs[b];
+      R.l = lv.l;
+      R.i = i;
+      R.a = st.a[i];
+      R.r = st.r[i];
+      R.p = R.a + R.r;
+      R.colour = lv.colour[i];
+      int off = 0;
+      for (int k = lv.nbr_ptr[i]; k < lv.nbr_ptr[i + 1]; k++) {
+        const int j = lv.nbr[k];
+        if (j == i) continue;
+        const char kind = st.elim[j] ? 'y' : 'x';
+        const int d = kind == 'x' ? st.a[j] : st.r[j];
+        R.blk.push_back({kind, j, d, off});
+        off += d;
+      }
+      R.blk.push_back({'y', i, R.r, off});
+      off += R.r;
+      R.nC = off;
+      const int p = R.p, nC = R.nC, a = R.a, r = R.r;
+      R.LU = f->store.alloc<double>((size_t)p * p);
+      R.piv = f->store.alloc<int>(p);
+      R.info = f->store.alloc<int>(1);
+      R.ERP = f->store.alloc<double>((size_t)nC * p);
+      R.G = f->store.alloc<double>((size_t)p * nC);
+      CK(cudaMemsetAsync(R.ERP, 0, sizeof(double) * (size_t)nC * p, s));
+      CK(cudaMemsetAsync(R.G, 0, sizeof(double) * (size_t)p * nC, s));
+      double* amax = scratch.alloc<double>(1);
+      // E(P,P) = [[X(i,i), U_i], [V_i^T, 0]]
+      cps.push_back(cp(X(st, lv, i, i), a, R.LU, p, a, a));
+      cps.push_back(cp(st.U[i], a, R.LU + (size_t)a * p, p, a, r));
+      cps.push_back(cp(st.V[i], a, R.LU + a, p, r, a, 1));
+      cps.push_back(cp_zero(R.LU + a + (size_t)a * p, p, r, r));
+      for (const BlockRef& B : R.blk) {
+        if (B.kind == 'y' && B.box == i) {
+          cps.push_back(cp_eye(R.G + a + (size_t)B.off * p, p, r, -1.0));
+          cps.push_back(cp_eye(R.ERP + B.off + (size_t)a * nC, nC, r, -1.0));
+        } else {
+          cps.push_back(cp(X(st, lv, i, B.box), a, R.G + (size_t)B.off * p, p, a, B.dim));
+          const int ldj = st.a[B.box];
+          cps.push_back(cp(X(st, lv, B.box, i), ldj, R.ERP + B.off, nC, B.dim, a));
+        }
+      }
+      lus.push_back({R.LU, p, p, R.piv, R.info, amax});
+      rss.push_back({R.LU, p, p, R.piv, R.G, p, nC});
+      S[b] = scratch.alloc<double>((size_t)nC * nC);
+      gs.push_back(gm(R.ERP, nC, 0, R.G, p, 0, S[b], nC, nC, nC, p, 1.0, 0.0));
+      f->info.flops_lu += 2.0 / 3.0 * p * (double)p * p;
+      f->info.flops_trsm += 2.0 * p * (double)p * nC;
+      f->info.flops_schur += 2.0 * nC * (double)p * nC;
+    }
+    run_copies(scratch, cps, s);
+    run_getrf(scratch, lus, s);
+    run_getrs(scratch, rss, s);
+    run_gemms(scratch, gs, s);
+    // scatter -S into edges; collect well-separated fill
+    struct Fill { int b, rb, cb; };
+    std::vector<Fill> fills;
+    cps.clear();
+    for (int b = 0; b < nbx; b++) {
+      const FRec& R = recs[b];
+      const int i = R.i, nC = R.nC;
+      for (int x = 0; x < (int)R.blk.size(); x++) {
+        const BlockRef& rb = R.blk[x];
+        for (int y = 0; y < (int)R.blk.size(); y++) {
+          const BlockRef& cb = R.blk[y];
+          const double* src = S[b] + rb.off + (size_t)cb.off * nC;
+          const int rj = rb.box, cj = cb.box;
+          if (rb.kind == 'y' && cb.kind == 'y') {
+            cps.push_back(cp(src, nC, Y(st, lv, rj, cj), st.rcap[rj], rb.dim, cb.dim, 0, -1.0, 1.0));
+          } else if (rb.kind == 'x' && cb.kind == 'y' && cj == i) {
+            cps.push_back(cp(src, nC, X(st, lv, rj, i), st.a[rj], rb.dim, cb.dim, 0, -1.0, 0.0));
+          } else if (rb.kind == 'y' && rj == i && cb.kind == 'x') {
+            cps.push_back(cp(src, nC, X(st, lv, i, cj), st.a[i], rb.dim, cb.dim, 0, -1.0, 0.0));
+          } else if (lv.is_nbr(rj, cj)) {
+            cps.push_back(cp(src, nC, X(st, lv, rj, cj), st.a[rj], rb.dim, cb.dim, 0, -1.0, 1.0));
+          } else {
+            fills.push_back({b, x, y});
+          }
+        }
+      }
+    }
+    run_copies(scratch, cps, s);
+    for (int b = 0; b < nbx; b++) st.elim[boxes[b]] = 1;
+    if (!fills.empty()) compress(st, lv, recs, S, fills);
+    for (auto& R : recs) f->recs.push_back(std::move(R));
+  }
+
+  template <class Fill>
+  void compress(FLevel& st, const LevelTopo& lv, const std::vector<FRec>& recs,
+                const std::vector<double*>& S, const std::vector<Fill>& fills) {
+    // recompressed boxes (uneliminated, with well-separated fill), in Morton order
+    std::map<int, int> slot;  // box -> index in J
+    std::vector<int> J;
+    for (const Fill& F : fills) {
+      const FRec& R = recs[F.b];
+      const int ks[2] = {F.rb, F.cb};
+      for (int k : ks)
+        if (R.blk[k].kind == 'x' && !slot.count(R.blk[k].box)) slot[R.blk[k].box] = 0;
+    }
+    for (auto& kv : slot) { kv.second = (int)J.size(); J.push_back(kv.first); }
+    const int nJ = (int)J.size();
+    std::vector<int> wU(nJ, 0), wV(nJ, 0);
+    for (int t = 0; t < nJ; t++) wU[t] = wV[t] = st.r[J[t]];
+    for (const Fill& F : fills) {
+      const FRec& R = recs[F.b];
+      const BlockRef &rb = R.blk[F.rb], &cb = R.blk[F.cb];
+      if (rb.kind == 'x') wU[slot[rb.box]] += cb.dim;
+      if (cb.kind == 'x') wV[slot[cb.box]] += rb.dim;
+    }
+    std::vector<double*> MU(nJ), MV(nJ), WU(nJ), WV(nJ), sU(nJ), sV(nJ);
+    std::vector<int> cU(nJ), cV(nJ);
+    std::vector<CopyTask> cps;
+    std::vector<SvdTask> svd;
+    int* d_r = scratch.alloc<int>(nJ);
+    for (int t = 0; t < nJ; t++) {
+      const int j = J[t], a = st.a[j], r = st.r[j];
+      MU[t] = scratch.alloc<double>((size_t)a * wU[t]);
+      MV[t] = scratch.alloc<double>((size_t)a * wV[t]);
+      WU[t] = scratch.alloc<double>((size_t)a * a);
+      WV[t] = scratch.alloc<double>((size_t)a * a);
+      sU[t] = scratch.alloc<double>(a);
+      sV[t] = scratch.alloc<double>(a);
+      cps.push_back(cp(st.U[j], a, MU[t], a, a, r, 0, 1.0, 0.0, st.SU[j]));
+      cps.push_back(cp(st.V[j], a, MV[t], a, a, r, 0, 1.0, 0.0, st.SV[j]));
+      cU[t] = cV[t] = r;
+    }
+    for (const Fill& F : fills) {  // [U Sigma_U | F_j1 | ..], [V Sigma_V | F_1j^T | ..]
+      const FRec& R = recs[F.b];
+      const BlockRef &rb = R.blk[F.rb], &cb = R.blk[F.cb];
+      const double* src = S[F.b] + rb.off + (size_t)cb.off * R.nC;
+      if (rb.kind == 'x') {
+        const int t = slot[rb.box];
+        const int a = st.a[rb.box];
+        cps.push_back(cp(src, R.nC, MU[t] + (size_t)cU[t] * a, a, rb.dim, cb.dim, 0, -1.0));
+        cU[t] += cb.dim;
+      }
+      if (cb.kind == 'x') {
+        const int t = slot[cb.box];
+        const int a = st.a[cb.box];
+        cps.push_back(cp(src, R.nC, MV[t] + (size_t)cV[t] * a, a, cb.dim, rb.dim, 1, -1.0));
+        cV[t] += rb.dim;
+      }
+    }
+    run_copies(scratch, cps, s);
+    std::vector<RankTask> rt;
+    for (int t = 0; t < nJ; t++) {
+      const int a = st.a[J[t]];
+      double* wk1 = a > 128 ? scratch.alloc<double>((size_t)a * a + (size_t)a * 32) : nullptr;
+      double* wk2 = a > 128 ? scratch.alloc<double>((size_t)a * a + (size_t)a * 32) : nullptr;
+      svd.push_back({MU[t], a, a, wU[t], WU[t], sU[t], wk1});
+      svd.push_back({MV[t], a, a, wV[t], WV[t], sV[t], wk2});
+      rt.push_back({sU[t], sV[t], a, st.rcap[J[t]], d_r + t, d_counters});
+      f->info.flops_lowrank += 4.0 * a * (double)a * (wU[t] + wV[t]);
+    }
+    run_svd_left(scratch, svd, s);
+    const RankTask* drt = upload(scratch, rt, s);
+    launch_rank(drt, nJ, tau, s);
+    std::vector<int> rn = read_ints(d_r, nJ);
+    // r_j = U_hat^T U_old, t_j = V_hat^T V_old
+    std::vector<double*> rm(nJ), tm(nJ);
+    std::vector<GemmTask> g;
+    for (int t = 0; t < nJ; t++) {
+      const int j = J[t], a = st.a[j];
+      rm[t] = scratch.alloc<double>((size_t)std::max(rn[t], 1) * std::max(st.r[j], 1));
+      tm[t] = scratch.alloc<double>((size_t)std::max(rn[t], 1) * std::max(st.r[j], 1));
+      g.push_back(gm(WU[t], a, 1, st.U[j], a, 0, rm[t], std::max(rn[t], 1), rn[t], st.r[j], a, 1.0, 0.0));
+      g.push_back(gm(WV[t], a, 1, st.V[j], a, 0, tm[t], std::max(rn[t], 1), rn[t], st.r[j], a, 1.0, 0.0));
+    }
+    run_gemms(scratch, g, s);
+    // Algorithm 3: K(j, q) <- r_j K(j, q), K(q, j) <- K(q, j) t_j^T (q in I_j)
+    std::set<std::pair<int, int>> edges;
+    for (int j : J)
+      for (int k = lv.far_ptr[j]; k < lv.far_ptr[j + 1]; k++) {
+        edges.insert({j, lv.far[k]});
+        edges.insert({lv.far[k], j});
+      }
+    auto rold = [&](int b) { return st.r[b]; };
+    auto rnew = [&](int b) { auto it = slot.find(b); return it == slot.end() ? st.r[b] : rn[it->second]; };
+    std::vector<GemmTask> p1, p2;
+    std::vector<CopyTask> c1, c2;
+    for (auto& e : edges) {
+      const int a = e.first, b = e.second;
+      double* Yab = Y(st, lv, a, b);
+      const int lda = st.rcap[a];
+      const int ra0 = rold(a), ra1 = rnew(a), rb0 = rold(b), rb1 = rnew(b);
+      double* T1 = scratch.alloc<double>((size_t)std::max(ra1, 1) * std::max(rb0, 1));
+      const int ldt = std::max(ra1, 1);
+      auto ia = slot.find(a), ib = slot.find(b);
+      if (ia != slot.end())
+        p1.push_back(gm(rm[ia->second], std::max(ra1, 1), 0, Yab, lda, 0, T1, ldt, ra1, rb0, ra0, 1.0, 0.0));
+      else
+        c1.push_back(cp(Yab, lda, T1, ldt, ra0, rb0));
+      if (ib != slot.end())
+        p2.push_back(gm(T1, ldt, 0, tm[ib->second], std::max(rb1, 1), 1, Yab, lda, ra1, rb1, rb0, 1.0, 0.0));
+      else
+        c2.push_back(cp(T1, ldt, Yab, lda, ra1, rb0));
+    }
+    // parent transfers: U(j, j-dagger) <- r_j U, V(j, j-dagger) <- t_j V (Eqs. U/V_parent_j_update)
+    if (lv.l > 2)
+      for (int t = 0; t < nJ; t++) {
+        const int j = J[t];
+        const int r0 = st.r[j], r1 = rn[t];
+        double* TU = scratch.alloc<double>((size_t)std::max(r1, 1) * nd);
+        double* TV = scratch.alloc<double>((size_t)std::max(r1, 1) * nd);
+        p1.push_back(gm(rm[t], std::max(r1, 1), 0, st.Upar[j], st.rcap[j], 0, TU, std::max(r1, 1), r1, nd, r0, 1.0, 0.0));
+        p1.push_back(gm(tm[t], std::max(r1, 1), 0, st.Vpar[j], st.rcap[j], 0, TV, std::max(r1, 1), r1, nd, r0, 1.0, 0.0));
+        c2.push_back(cp(TU, std::max(r1, 1), st.Upar[j], st.rcap[j], r1, nd));
+        c2.push_back(cp(TV, std::max(r1, 1), st.Vpar[j], st.rcap[j], r1, nd));
+      }
+    run_gemms(scratch, p1, s);
+    run_copies(scratch, c1, s);
+    run_gemms(scratch, p2, s);
+    run_copies(scratch, c2, s);
+    // redirect the fill through the new bases (Eq. K_kj_update)
+    std::vector<GemmTask> q1, q2;
+    for (const Fill& F : fills) {
+      const FRec& R = recs[F.b];
+      const BlockRef &rb = R.blk[F.rb], &cb = R.blk[F.cb];
+      const double* src = S[F.b] + rb.off + (size_t)cb.off * R.nC;
+      const int nC = R.nC;
+      double* Yt = Y(st, lv, rb.box, cb.box);
+      const int ldy = st.rcap[rb.box];
+      if (rb.kind == 'x' && cb.kind == 'x') {
+        const int tj = slot[rb.box], tk = slot[cb.box];
+        const int rj = rn[tj], rk = rn[tk];
+        double* T = scratch.alloc<double>((size_t)std::max(rj, 1) * cb.dim);
+        q1.push_back(gm(WU[tj], st.a[rb.box], 1, src, nC, 0, T, std::max(rj, 1), rj, cb.dim, rb.dim, -1.0, 0.0));
+        q2.push_back(gm(T, std::max(rj, 1), 0, WV[tk], st.a[cb.box], 0, Yt, ldy, rj, rk, cb.dim, 1.0, 1.0));
+      } else if (rb.kind == 'x') {
+        const int tj = slot[rb.box];
+        q1.push_back(gm(WU[tj], st.a[rb.box], 1, src, nC, 0, Yt, ldy, rn[tj], cb.dim, rb.dim, -1.0, 1.0));
+      } else {
+        const int tk = slot[cb.box];
+        q1.push_back(gm(src, nC, 0, WV[tk], st.a[cb.box], 0, Yt, ldy, rb.dim, rn[tk], cb.dim, -1.0, 1.0));
+      }
+    }
+    run_gemms(scratch, q1, s);
+    run_gemms(scratch, q2, s);
+    // new bases and weights (Algorithm 3, lines 1-2)
+    cps.clear();
+    for (int t = 0; t < nJ; t++) {
+      const int j = J[t], a = st.a[j], r1 = rn[t];
+      cps.push_back(cp(WU[t], a, st.U[j], a, a, r1));
+      cps.push_back(cp(WV[t], a, st.V[j], a, a, r1));
+      cps.push_back(cp(sU[t], 1, st.SU[j], 1, r1, 1));
+      cps.push_back(cp(sV[t], 1, st.SV[j], 1, r1, 1));
+    }
+    run_copies(scratch, cps, s);
+    for (int t = 0; t < nJ; t++) st.r[J[t]] = rn[t];
+  }
+
+  // -------------------------------------------------------------------------
+  // merge (Eqs. y_merge, U_merge, V_merge, K_merge)
+  // -------------------------------------------------------------------------
+  void merge(FLevel& st, const LevelTopo& lv, FLevel& nst, const LevelTopo& pv) {
+    nst.a.assign(pv.nb, 0);
+    std::vector<std::vector<int>> coff(pv.nb);
+    for (int p = 0; p < pv.nb; p++) {
+      int off = 0;
+      for (int c = pv.cb[p]; c < pv.ce[p]; c++) { coff[p].push_back(off); off += st.r[c]; }
+      nst.a[p] = off;
+    }
+    alloc_level(nst, pv);
+    nst.Uraw.resize(pv.nb);
+    nst.Vraw.resize(pv.nb);
+    std::vector<CopyTask> cps;
+    for (int p = 0; p < pv.nb; p++) {
+      const int ap = nst.a[p];
+      nst.Uraw[p] = nst.mem.alloc<double>((size_t)std::max(ap, 1) * nd);
+      nst.Vraw[p] = nst.mem.alloc<double>((size_t)std::max(ap, 1) * nd);
+      for (int c = pv.cb[p]; c < pv.ce[p]; c++) {
+        const int o = coff[p][c - pv.cb[p]];
+        cps.push_back(cp(st.Upar[c], st.rcap[c], nst.Uraw[p] + o, ap, st.r[c], nd));
+        cps.push_back(cp(st.Vpar[c], st.rcap[c], nst.Vraw[p] + o, ap, st.r[c], nd));
+      }
+      for (int k = pv.nbr_ptr[p]; k < pv.nbr_ptr[p + 1]; k++) {
+        const int q = pv.nbr[k];
+        double* Xpq = nst.X[k];
+        for (int c = pv.cb[p]; c < pv.ce[p]; c++)
+          for (int d = pv.cb[q]; d < pv.ce[q]; d++) {
+            const int oc = coff[p][c - pv.cb[p]], od = coff[q][d - pv.cb[q]];
+            cps.push_back(cp(Y(st, lv, c, d), st.rcap[c], Xpq + oc + (size_t)od * ap, ap, st.r[c], st.r[d]));
+          }
+      }
+    }
+    scratch.reset();
+    run_copies(scratch, cps, s);
+    CK(cudaStreamSynchronize(s));
+    scratch.reset();
+  }
+
+  void top(FLevel& st, const LevelTopo& lv) {
+    std::vector<int> off(st.nb + 1, 0);
+    for (int i = 0; i < st.nb; i++) off[i + 1] = off[i] + st.r[i];
+    const int n = off[st.nb];
+    f->top_n = n;
+    f->info.top_size = n;
+    if (n == 0) return;
+    f->top_LU = f->store.alloc<double>((size_t)n * n);
+    f->top_piv = f->store.alloc<int>(n);
+    f->top_info = f->store.alloc<int>(1);
+    std::vector<CopyTask> cps;
+    for (int i = 0; i < st.nb; i++)
+      for (int j = 0; j < st.nb; j++) {
+        const int k = lv.yslot(i, j);
+        if (k < 0) throw Error(IFMM_ERR_CUDA, "internal: top system is not dense");
+        cps.push_back(cp(st.Y[k], st.rcap[i], f->top_LU + off[i] + (size_t)off[j] * n, n, st.r[i], st.r[j]));
+      }
+    scratch.reset();
+    run_copies(scratch, cps, s);
+    double* amax = scratch.alloc<double>(1);
+    run_getrf(scratch, {LuTask{f->top_LU, n, n, f->top_piv, f->top_info, amax}}, s);
+    f->info.flops_top += 2.0 / 3.0 * n * (double)n * n;
+    CK(cudaStreamSynchronize(s));
+  }
+
+  void run() {
+    const ifmm_options& o = sys->opt;
+    auto t0 = Clock::now();
+    const int L = sys->L;
+    f->info.levels = L;
+    d_counters = f->store.alloc<int>(4);
+    CK(cudaMemsetAsync(d_counters, 0, 4 * sizeof(int), s));
+    if (L == 0) {  // no tree: one dense LU of A
+      const int N = (int)sys->N;
+      f->dense_LU = f->store.alloc<double>((size_t)N * N);
+      f->dense_piv = f->store.alloc<int>(N);
+      f->dense_info = f->store.alloc<int>(1);
+      P2PTask t{0, N, 0, N, 0};
+      const P2PTask* d = upload(scratch, std::vector<P2PTask>{t}, s);
+      launch_p2p_blocks(sys->ks, sys->dim, sys->pts_tree, d, 1, f->dense_LU, s);
+      double* amax = scratch.alloc<double>(1);
+      run_getrf(scratch, {LuTask{f->dense_LU, N, N, f->dense_piv, f->dense_info, amax}}, s);
+      CK(cudaStreamSynchronize(s));
+      f->info.flops_top = 2.0 / 3.0 * N * (double)N * N;
+      f->info.seconds_top = since(t0);
+      return;
+    }
+    if (o.tau_override > 0.0) {
+      tau = o.tau_override;
+    } else if (o.eps == 0.0) {
+      tau = 0.0;
+    } else {
+      auto ts = Clock::now();
+      if (std::isnan(sys->sigma0)) sys->sigma0 = system_sigma0(sys, s, &sys->sigma0_iters);
+      f->info.seconds_sigma0 = since(ts);
+      tau = o.eps * sys->sigma0;
+    }
+    f->info.sigma0 = sys->sigma0;
+    f->info.sigma0_iters = sys->sigma0_iters;
+    f->info.tau = tau;
+    cap_global = o.rank_cap > 0 ? o.rank_cap : (tau == 0.0 ? (1 << 30) : 2 * nd);
+    f->rank.assign(L + 1, {});
+    f->yoff.assign(L + 1, {});
+    auto st = std::make_unique<FLevel>();
+    const LevelTopo& leaf = sys->lv[L];
+    st->a.resize(leaf.nb);
+    for (int i = 0; i < leaf.nb; i++) st->a[i] = leaf.p1[i] - leaf.p0[i];
+    alloc_level(*st, leaf);
+    // X blocks of the leaves are the near-field blocks (same slot order and ld)
+    {
+      long long tot = 0;
+      for (int i = 0; i < leaf.nb; i++)
+        for (int k = leaf.nbr_ptr[i]; k < leaf.nbr_ptr[i + 1]; k++)
+          tot += (long long)st->a[i] * st->a[leaf.nbr[k]];
+      if (tot > 0)
+        CK(cudaMemcpyAsync(st->X[0], sys->p2p, tot * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+    st->Uraw.resize(leaf.nb);
+    st->Vraw.resize(leaf.nb);
+    for (int i = 0; i < leaf.nb; i++) st->Uraw[i] = st->Vraw[i] = ops.leafU + ops.uoff[i];
+    for (int l = L; l >= 2; l--) {
+      const LevelTopo& lv = sys->lv[l];
+      auto ti = Clock::now();
+      init_basis(*st, lv);
+      f->info.seconds_init += since(ti);
+      auto te = Clock::now();
+      int ncol = 1;
+      for (int d = 0; d < dim; d++) ncol *= 3;
+      for (int c = 0; c < ncol; c++) {
+        std::vector<int> boxes;
+        for (int i = 0; i < lv.nb; i++)
+          if (lv.colour[i] == c) boxes.push_back(i);
+        if (!boxes.empty()) eliminate_colour(*st, lv, boxes);
+      }
+      CK(cudaStreamSynchronize(s));
+      f->info.seconds_elim += since(te);
+      f->rank[l] = st->r;
+      f->yoff[l].assign(lv.nb + 1, 0);
+      for (int i = 0; i < lv.nb; i++) f->yoff[l][i + 1] = f->yoff[l][i] + st->r[i];
+      int mx = 0;
+      double av = 0.0;
+      for (int v : st->r) { mx = std::max(mx, v); av += v; }
+      if (l < 32) {
+        f->info.max_rank[l] = mx;
+        f->info.avg_rank[l] = lv.nb ? av / lv.nb : 0.0;
+      }
+      if (l > 2) {
+        auto tm = Clock::now();
+        auto nst = std::make_unique<FLevel>();
+        merge(*st, lv, *nst, sys->lv[l - 1]);
+        st = std::move(nst);
+        f->info.seconds_elim += since(tm);
+      }
+    }
+    auto tt = Clock::now();
+    top(*st, sys->lv[2]);
+    f->info.seconds_top = since(tt);
+    std::vector<int> cnt = read_ints(d_counters, 4);
+    f->info.rank_capped = cnt[0];
+  }
+};
+
+ifmm_factorization* factor_create(ifmm_system* sys, cudaStream_t s) {
+  auto* f = new ifmm_factorization();
+  f->sys = sys;
+  try {
+    Factorizer fz(sys, f, s);
+    fz.run();
+    // singular pivot tests
+    int sing = 0;
+    std::vector<int> h;
+    for (const FRec& R : f->recs) {
+      int v = 0;
+      CK(cudaMemcpyAsync(&v, R.info, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      sing += v != 0;
+    }
+    for (int* p : {f->top_info, f->dense_info})
+      if (p) {
+        int v = 0;
+        CK(cudaMemcpyAsync(&v, p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        sing += v != 0;
+      }
+    f->info.singular_pivots = sing;
+    f->info.factor_bytes = (long long)f->store.held;
+    return f;
+  } catch (...) {
+    delete f;
+    throw;
+  }
+}
+
+}  // namespace ifmm

@@ -1,0 +1,306 @@
+// internal.cuh -- shared types of the IFMM CUDA library (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <stdexcept>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/ifmm.h"
+
+namespace ifmm {
+
+struct Error : std::runtime_error {
+  ifmm_status st;
+  Error(ifmm_status s, const std::string& m) : std::runtime_error(m), st(s) {}
+};
+
+inline void cuda_check(cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    throw Error(IFMM_ERR_OOM, std::string(what) + ": out of device memory");
+  }
+  if (e != cudaSuccess) throw Error(IFMM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+#define CK(x) ::ifmm::cuda_check((x), #x)
+// every launch site of the library is followed by CK_LAUNCH, which also counts it
+unsigned long long& launch_counter();
+#define CK_LAUNCH(name) \
+  (++::ifmm::launch_counter(), ::ifmm::cuda_check(cudaGetLastError(), name))
+
+inline void require(bool ok, const std::string& m) {
+  if (!ok) throw Error(IFMM_ERR_INVALID_ARG, m);
+}
+
+// ---------------------------------------------------------------------------
+// Optional host-side bounds validation (IFMM_VALIDATE=1): every device range
+// handed out by an Arena, and every caller buffer, is registered; before a
+// launch the task builders check each descriptor's extent against them and
+// throw instead of launching an out-of-range access.
+// ---------------------------------------------------------------------------
+struct Ranges {
+  static bool on() {
+    static const bool v = [] {
+      const char* e = std::getenv("IFMM_VALIDATE");
+      return e && e[0] == '1';
+    }();
+    return v;
+  }
+  static std::map<uintptr_t, size_t>& map() {
+    static std::map<uintptr_t, size_t> m;
+    return m;
+  }
+  static std::mutex& mu() {
+    static std::mutex m;
+    return m;
+  }
+  static void add(const void* p, size_t n) {
+    if (!on() || !p) return;
+    std::lock_guard<std::mutex> g(mu());
+    map()[(uintptr_t)p] = n;
+  }
+  static void remove(const void* p) {
+    if (!on() || !p) return;
+    std::lock_guard<std::mutex> g(mu());
+    map().erase((uintptr_t)p);
+  }
+  static void check(const void* p, size_t bytes, const char* what) {
+    if (!on() || bytes == 0) return;
+    std::lock_guard<std::mutex> g(mu());
+    auto& m = map();
+    auto it = m.upper_bound((uintptr_t)p);
+    bool ok = false;
+    if (it != m.begin()) {
+      --it;
+      ok = (uintptr_t)p >= it->first && (uintptr_t)p + bytes <= it->first + it->second;
+    }
+    if (!ok) throw Error(IFMM_ERR_CUDA, std::string("bounds check failed: ") + what);
+  }
+};
+// bytes spanned by a column-major rows x cols matrix with leading dimension ld
+inline size_t mat_bytes(long long rows, long long cols, long long ld, size_t elem = 8) {
+  if (rows <= 0 || cols <= 0) return 0;
+  if (cols > 1 && ld < rows)
+    throw Error(IFMM_ERR_CUDA, "bounds check failed: leading dimension < rows");
+  return (size_t)((cols - 1) * ld + rows) * elem;
+}
+struct ScopedRange {
+  const void* p;
+  ScopedRange(const void* q, size_t n) : p(q) { Ranges::add(q, n); }
+  ~ScopedRange() { Ranges::remove(p); }
+};
+
+// ---------------------------------------------------------------------------
+// Launch profiler (profile.cu): Prof p("k_gemm", flops, bytes, stream) before
+// a launch, destroyed after it, records an event pair when profiling is on.
+// ---------------------------------------------------------------------------
+namespace prof {
+bool enabled();
+void* begin(const char* name, double flops, double bytes, cudaStream_t s);
+void end(void* token, cudaStream_t s);
+void start();
+int stop(ifmm_kernel_stat* out, int capacity);
+}  // namespace prof
+struct Prof {
+  void* tok;
+  cudaStream_t s;
+  Prof(const char* name, double flops, double bytes, cudaStream_t st)
+      : tok(prof::enabled() ? prof::begin(name, flops, bytes, st) : nullptr), s(st) {}
+  ~Prof() { if (tok) prof::end(tok, s); }
+};
+
+// ---------------------------------------------------------------------------
+// Device memory: a chunked bump allocator.  Blocks are 256-byte aligned.
+// reset() rewinds without freeing, so per-colour scratch reuses its chunks.
+// ---------------------------------------------------------------------------
+struct Arena {
+  size_t chunk_bytes = size_t(256) << 20;
+  std::vector<std::pair<char*, size_t>> chunks;
+  size_t cur = 0;       // index of the chunk being filled
+  size_t off = 0;       // bytes used in it
+  size_t held = 0;      // bytes of device memory held
+  size_t high = 0;      // bytes handed out since the last reset
+  Arena() = default;
+  Arena(const Arena&) = delete;
+  Arena& operator=(const Arena&) = delete;
+  ~Arena() { release(); }
+  char* alloc_bytes(size_t bytes) {
+    bytes = (bytes + 255) & ~size_t(255);
+    if (bytes == 0) bytes = 256;
+    while (cur < chunks.size()) {
+      if (off + bytes <= chunks[cur].second) {
+        char* p = chunks[cur].first + off;
+        off += bytes;
+        high += bytes;
+        return p;
+      }
+      cur++;
+      off = 0;
+    }
+    size_t sz = bytes > chunk_bytes ? bytes : chunk_bytes;
+    char* p = nullptr;
+    CK(cudaMalloc(&p, sz));
+    Ranges::add(p, sz);
+    chunks.push_back({p, sz});
+    held += sz;
+    cur = chunks.size() - 1;
+    off = bytes;
+    high += bytes;
+    return p;
+  }
+  template <class T>
+  T* alloc(size_t n) { return reinterpret_cast<T*>(alloc_bytes(n * sizeof(T))); }
+  void reset() { cur = 0; off = 0; high = 0; }
+  void release() {
+    for (auto& c : chunks) {
+      Ranges::remove(c.first);
+      cudaFree(c.first);
+    }
+    chunks.clear();
+    cur = off = held = high = 0;
+  }
+};
+
+// A device copy of a host vector of POD tasks.
+template <class T>
+T* upload(Arena& ar, const std::vector<T>& v, cudaStream_t s) {
+  if (v.empty()) return nullptr;
+  T* d = ar.alloc<T>(v.size());
+  CK(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+  return d;
+}
+
+// ---------------------------------------------------------------------------
+// Batched dense kernels (kernels_linalg.cu).  All matrices are FP64
+// column-major; element (r, c) of a matrix with leading dimension ld is
+// p[r + c * ld].
+// ---------------------------------------------------------------------------
+
+// dst(r, c) = beta * dst(r, c) + alpha * S(r, c) * (cscale ? cscale[c] : 1)
+// S = src(r, c), src(c, r) (trans), the identity (kind 1) or zero (kind 2).
+// beta == 0 never reads dst.
+struct CopyTask {
+  const double* src;
+  double* dst;
+  const double* cscale;
+  int lds, ldd, rows, cols;
+  int trans, kind;
+  double alpha, beta;
+};
+void launch_copy(const CopyTask* d_tasks, int ntasks, cudaStream_t s);
+void validate(const CopyTask& t);
+
+// C = alpha op(A) op(B) + beta C; beta == 0 never reads C.
+struct GemmTask {
+  const double* A;
+  const double* B;
+  double* C;
+  int lda, ldb, ldc;
+  int M, N, K;
+  int transA, transB;
+  double alpha, beta;
+};
+struct GemmTile {
+  int task, m0, n0;
+};
+void validate(const GemmTask& t);
+// Host helper: append the 64x64 output tiles of task `t`.
+void gemm_tiles(const GemmTask& t, int task_index, std::vector<GemmTile>& tiles);
+void launch_gemm(const GemmTask* d_tasks, const GemmTile* d_tiles, int ntiles, cudaStream_t s,
+                 double flops = 0.0);
+// Convenience: run a host list of GEMM tasks (uploads into `ar`).
+void run_gemms(Arena& ar, const std::vector<GemmTask>& tasks, cudaStream_t s);
+
+// Batched LU with partial pivoting (right-looking, panel width LU_NB).
+struct LuTask {
+  double* A;
+  int lda, n;
+  int* piv;      // n entries, 0-based global row swapped with row k at step k
+  int* info;     // 0, or 1 + first column whose pivot failed the test
+  double* amax;  // scratch: max |A| before factorisation
+};
+constexpr int LU_NB = 64;
+void run_getrf(Arena& ar, const std::vector<LuTask>& tasks, cudaStream_t s);
+
+// X = A^-1 B in place of B, with A = P L U from run_getrf.
+struct RsTask {
+  const double* LU;
+  int lda, n;
+  const int* piv;
+  double* B;
+  int ldb, ncols;
+};
+void run_getrs(Arena& ar, const std::vector<RsTask>& tasks, cudaStream_t s);
+
+// Pre-uploaded form of run_getrs: every launch's task arrays live in the
+// arena given to plan_getrs, so exec_getrs can be replayed without host work.
+struct GemmLaunch {
+  const GemmTask* tasks = nullptr;
+  const GemmTile* tiles = nullptr;
+  int ntiles = 0;
+  double flops = 0.0;
+};
+GemmLaunch plan_gemms(Arena& ar, const std::vector<GemmTask>& tasks, cudaStream_t s);
+struct GetrsPlan {
+  const RsTask* d = nullptr;
+  int nt = 0, nmax = 0, gy = 1;
+  std::vector<GemmLaunch> fwd, bwd;  // per panel, forward / backward order
+};
+GetrsPlan plan_getrs(Arena& ar, const std::vector<RsTask>& tasks, cudaStream_t s);
+void exec_getrs(const GetrsPlan& p, cudaStream_t s);
+
+// Left singular vectors and values of M (a x w, a <= w after zero padding is
+// implied): W (a x a, ld a) and sigma (a), sorted by decreasing sigma.
+// work: a*w + a*a doubles of scratch (only used when the matrix is too big for
+// shared memory).
+struct SvdTask {
+  const double* M;
+  int ldm, a, w;
+  double* W;
+  double* sigma;
+  double* work;
+};
+void run_svd_left(Arena& ar, const std::vector<SvdTask>& tasks, cudaStream_t s);
+
+// r_out[j] = min(max(#(sigU > tau), #(sigV > tau)), full, cap) (tau <= 0: full)
+struct RankTask {
+  const double* sigU;
+  const double* sigV;
+  int full;  // number of singular values available (= a)
+  int cap;
+  int* out;
+  int* capped;  // incremented when the cap binds
+};
+void launch_rank(const RankTask* d, int n, double tau, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Block-row sparse products (kernels_ops.cu): for each output row-block
+// y = beta y + sum_e alpha_e op(A_e) x_e, nrhs columns.  A == nullptr means
+// the identity.  Column c of x / y sits at x + c * ldx / y + c * ldy.
+// ---------------------------------------------------------------------------
+struct SpRow {
+  double* y;
+  long long ldy;
+  int m;
+  int e0, ne;
+  double beta;
+};
+struct SpEnt {
+  const double* A;
+  const double* x;
+  long long ldx;
+  int lda, k, transA;
+  double alpha;
+};
+void launch_spmm(const SpRow* rows, int nrows, const SpEnt* ents, int nrhs, cudaStream_t s,
+                 double flops = 0.0, double bytes = 0.0);
+void validate_spmm(const std::vector<SpRow>& rows, const std::vector<SpEnt>& ents, int nrhs);
+
+}  // namespace ifmm

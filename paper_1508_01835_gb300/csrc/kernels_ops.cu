@@ -1,0 +1,288 @@
+// kernels_ops.cu -- kernel evaluation, Chebyshev operators and block-sparse
+// products of the IFMM library.
+//
+// Operators (Sec. 2.1, Sec. 3): the leaf interpolation U_i = V_i (L2P / P2M),
+// the child-to-parent transfer T_c (L2L, its transpose M2M), the M2L blocks
+// K_iq between Chebyshev nodes of well-separated boxes, and the exact
+// near-field blocks S_ij (P2P).  The interpolant of the black-box FMM the
+// paper cites is S_n(x, t) = 1/n + (2/n) sum_{k=1}^{n-1} T_k(x) T_k(t).
+#include "kernels_ops.cuh"
+
+namespace ifmm {
+
+__device__ __forceinline__ double kernel_value(const KSpec& k, double r) {
+  if (r == 0.0) return k.diag;
+  if (k.kind == IFMM_K_INV_R) return 1.0 / r;
+  if (k.kind == IFMM_K_GAUSSIAN) return exp(-(r * r) / (2.0 * k.param * k.param));
+  return (r < k.param) ? r / k.param : k.param / r;  // Eq. (K_ij)
+}
+
+__device__ __forceinline__ double dist(const double* x, const double* y, int dim) {
+  double s = 0.0;
+  for (int d = 0; d < dim; d++) {
+    const double t = x[d] - y[d];
+    s += t * t;
+  }
+  return sqrt(s);
+}
+
+// one-dimensional interpolant S_n(x, t_a)
+__device__ double cheb_S1(const ChebSpec& c, double x, int a) {
+  const double t = c.t[a];
+  double s = 1.0 / c.n;
+  if (c.n > 1) {
+    double tx0 = 1.0, tx1 = x, tt0 = 1.0, tt1 = t;
+    s += (2.0 / c.n) * tx1 * tt1;
+    for (int k = 2; k < c.n; k++) {
+      const double tx2 = 2.0 * x * tx1 - tx0, tt2 = 2.0 * t * tt1 - tt0;
+      s += (2.0 / c.n) * tx2 * tt2;
+      tx0 = tx1; tx1 = tx2; tt0 = tt1; tt1 = tt2;
+    }
+  }
+  return s;
+}
+
+// U[p, a] of every leaf: one thread per (point, node)
+__global__ void k_leaf_interp(ChebSpec c, int dim, const double* __restrict__ pts_tree,
+                              const LeafGeom* __restrict__ leaves, int nleaves,
+                              double* __restrict__ U) {
+  const int i = blockIdx.x;
+  if (i >= nleaves) return;
+  const LeafGeom g = leaves[i];
+  const int m = g.p1 - g.p0;
+  for (int e = threadIdx.x; e < m * c.nd; e += blockDim.x) {
+    const int p = e % m, a = e / m;
+    const double* x = pts_tree + (size_t)(g.p0 + p) * dim;
+    double v = 1.0;
+    int aa = a;
+    for (int d = 0; d < dim; d++) {
+      const double xi = (x[d] - g.centre[d]) / g.h;
+      v *= cheb_S1(c, xi, aa % c.n);
+      aa /= c.n;
+    }
+    U[g.uoff + e] = v;
+  }
+}
+
+// T_c[a, b] = prod_d S_n(shift_d + t_{a_d} / 2, t_{b_d}), shift = +-1/2
+__global__ void k_transfer(ChebSpec c, int dim, double* __restrict__ T) {
+  const int child = blockIdx.x;
+  const int nd = c.nd;
+  for (int e = threadIdx.x; e < nd * nd; e += blockDim.x) {
+    const int a = e % nd, b = e / nd;
+    int aa = a, bb = b;
+    double v = 1.0;
+    for (int d = 0; d < dim; d++) {
+      const double shift = ((child >> d) & 1) ? 0.5 : -0.5;
+      v *= cheb_S1(c, shift + 0.5 * c.t[aa % c.n], bb % c.n);
+      aa /= c.n;
+      bb /= c.n;
+    }
+    T[(size_t)child * nd * nd + e] = v;
+  }
+}
+
+// M2L table of one level: K_off[a, b] = K(|x_a - y_b|) with x_a = h t_a and
+// y_b = 2 h delta + h t_b, delta in [-3, 3]^dim (offset index sum (delta_d+3) 7^d)
+__global__ void k_m2l_table(ChebSpec c, int dim, KSpec ks, double h, double* __restrict__ K) {
+  const int o = blockIdx.x;
+  int delta[3] = {0, 0, 0};
+  int oo = o;
+  for (int d = 0; d < dim; d++) { delta[d] = oo % 7 - 3; oo /= 7; }
+  const int nd = c.nd;
+  for (int e = threadIdx.x; e < nd * nd; e += blockDim.x) {
+    const int a = e % nd, b = e / nd;
+    double xa[3], yb[3];
+    int aa = a, bb = b;
+    for (int d = 0; d < dim; d++) {
+      xa[d] = h * c.t[aa % c.n];
+      yb[d] = 2.0 * h * delta[d] + h * c.t[bb % c.n];
+      aa /= c.n;
+      bb /= c.n;
+    }
+    K[(size_t)o * nd * nd + e] = kernel_value(ks, dist(xa, yb, dim));
+  }
+}
+
+// near-field blocks S_ij, one CTA per (i, j) pair
+__global__ void k_p2p_blocks(KSpec ks, int dim, const double* __restrict__ pts_tree,
+                             const P2PTask* __restrict__ tasks, double* __restrict__ S) {
+  const P2PTask t = tasks[blockIdx.x];
+  const int mi = t.i1 - t.i0, mj = t.j1 - t.j0;
+  for (int e = threadIdx.x; e < mi * mj; e += blockDim.x) {
+    const int r = e % mi, c = e / mi;
+    const int gi = t.i0 + r, gj = t.j0 + c;
+    const double v = (gi == gj) ? ks.diag
+                                : kernel_value(ks, dist(pts_tree + (size_t)gi * dim,
+                                                        pts_tree + (size_t)gj * dim, dim));
+    S[t.off + e] = v;
+  }
+}
+
+// y = A x over all points (direct sum), user order, one thread per target
+__global__ void __launch_bounds__(256) k_direct(KSpec ks, int dim, const double* __restrict__ pts,
+                                                long long N, const double* __restrict__ x,
+                                                long long ldx, double* __restrict__ y,
+                                                long long ldy, int col) {
+  __shared__ double sp[256 * 3];
+  __shared__ double sx[256];
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double xi[3] = {0, 0, 0};
+  if (i < N)
+    for (int d = 0; d < dim; d++) xi[d] = pts[i * dim + d];
+  double acc = 0.0;
+  const double* xc = x + (long long)col * ldx;
+  for (long long j0 = 0; j0 < N; j0 += 256) {
+    const long long j = j0 + threadIdx.x;
+    if (j < N) {
+      for (int d = 0; d < dim; d++) sp[threadIdx.x * 3 + d] = pts[j * dim + d];
+      sx[threadIdx.x] = xc[j];
+    }
+    __syncthreads();
+    const int nj = (int)min((long long)256, N - j0);
+    if (i < N) {
+      for (int q = 0; q < nj; q++) {
+        const long long gj = j0 + q;
+        const double v = (gj == i) ? ks.diag : kernel_value(ks, dist(xi, sp + q * 3, dim));
+        acc += v * sx[q];
+      }
+    }
+    __syncthreads();
+  }
+  if (i < N) y[(long long)col * ldy + i] = acc;
+}
+
+// block-row sparse product: one CTA per output row-block
+__global__ void __launch_bounds__(128) k_spmm(const SpRow* __restrict__ rows,
+                                              const SpEnt* __restrict__ ents, int nrhs) {
+  const SpRow R = rows[blockIdx.x];
+  for (int c = 0; c < nrhs; c++) {
+    for (int r = threadIdx.x; r < R.m; r += blockDim.x) {
+      double acc = 0.0;
+      for (int e = R.e0; e < R.e0 + R.ne; e++) {
+        const SpEnt E = ents[e];
+        const double* x = E.x + (long long)c * E.ldx;
+        double s = 0.0;
+        if (!E.A) {
+          s = x[r];
+        } else if (!E.transA) {
+          const double* a = E.A + r;
+          for (int q = 0; q < E.k; q++) s += a[(long long)q * E.lda] * x[q];
+        } else {
+          const double* a = E.A + (long long)r * E.lda;
+          for (int q = 0; q < E.k; q++) s += a[q] * x[q];
+        }
+        acc += E.alpha * s;
+      }
+      double* y = R.y + (long long)c * R.ldy + r;
+      *y = (R.beta == 0.0) ? acc : R.beta * (*y) + acc;
+    }
+  }
+}
+
+void validate_spmm(const std::vector<SpRow>& rows, const std::vector<SpEnt>& ents, int nrhs) {
+  if (!Ranges::on()) return;
+  for (const SpRow& R : rows) {
+    Ranges::check(R.y, mat_bytes(R.m, nrhs, R.ldy), "spmm y");
+    for (int e = R.e0; e < R.e0 + R.ne; e++) {
+      const SpEnt& E = ents.at(e);
+      if (!E.A) {
+        if (E.k != R.m) throw Error(IFMM_ERR_CUDA, "bounds check failed: identity entry size");
+        Ranges::check(E.x, mat_bytes(R.m, nrhs, E.ldx), "spmm x (identity)");
+        continue;
+      }
+      Ranges::check(E.A, E.transA ? mat_bytes(E.k, R.m, E.lda) : mat_bytes(R.m, E.k, E.lda),
+                    "spmm A");
+      Ranges::check(E.x, mat_bytes(E.k, nrhs, E.ldx), "spmm x");
+    }
+  }
+}
+
+void launch_spmm(const SpRow* rows, int nrows, const SpEnt* ents, int nrhs, cudaStream_t s,
+                 double flops, double bytes) {
+  if (nrows <= 0 || nrhs <= 0) return;
+  Prof p("k_spmm", flops * nrhs, bytes, s);
+  k_spmm<<<nrows, 128, 0, s>>>(rows, ents, nrhs);
+  CK_LAUNCH("k_spmm");
+}
+
+// out[t + c ld_out] = in[perm[t] + c ld_in]   (gather: user -> tree order)
+__global__ void k_gather_rows(const long long* __restrict__ perm, long long N,
+                              const double* __restrict__ in, long long ldi,
+                              double* __restrict__ out, long long ldo, int ncols) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N) return;
+  const long long p = perm[t];
+  for (int c = 0; c < ncols; c++) out[t + c * ldo] = in[p + c * ldi];
+}
+
+// out[perm[t] + c ld_out] = in[t + c ld_in]   (scatter: tree -> user order)
+__global__ void k_scatter_rows(const long long* __restrict__ perm, long long N,
+                               const double* __restrict__ in, long long ldi,
+                               double* __restrict__ out, long long ldo, int ncols) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N) return;
+  const long long p = perm[t];
+  for (int c = 0; c < ncols; c++) out[p + c * ldo] = in[t + c * ldi];
+}
+
+__global__ void k_permute_points(const long long* __restrict__ perm, long long N, int dim,
+                                 const double* __restrict__ in, double* __restrict__ out) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N) return;
+  const long long p = perm[t];
+  for (int d = 0; d < dim; d++) out[t * dim + d] = in[p * dim + d];
+}
+
+void launch_permute_points(const long long* perm, long long N, int dim, const double* in,
+                           double* out, cudaStream_t s) {
+  if (N <= 0) return;
+  k_permute_points<<<(int)((N + 255) / 256), 256, 0, s>>>(perm, N, dim, in, out);
+  CK_LAUNCH("k_permute_points");
+}
+
+void launch_leaf_interp(ChebSpec c, int dim, const double* pts_tree, const LeafGeom* leaves,
+                        int nleaves, double* U, cudaStream_t s) {
+  if (nleaves <= 0) return;
+  k_leaf_interp<<<nleaves, 256, 0, s>>>(c, dim, pts_tree, leaves, nleaves, U);
+  CK_LAUNCH("k_leaf_interp");
+}
+void launch_transfer(ChebSpec c, int dim, double* T, cudaStream_t s) {
+  k_transfer<<<1 << dim, 256, 0, s>>>(c, dim, T);
+  CK_LAUNCH("k_transfer");
+}
+void launch_m2l_table(ChebSpec c, int dim, KSpec ks, double h, double* K, cudaStream_t s) {
+  int no = 1;
+  for (int d = 0; d < dim; d++) no *= 7;
+  k_m2l_table<<<no, 256, 0, s>>>(c, dim, ks, h, K);
+  CK_LAUNCH("k_m2l_table");
+}
+void launch_p2p_blocks(KSpec ks, int dim, const double* pts_tree, const P2PTask* tasks, int n,
+                       double* S, cudaStream_t s) {
+  if (n <= 0) return;
+  k_p2p_blocks<<<n, 256, 0, s>>>(ks, dim, pts_tree, tasks, S);
+  CK_LAUNCH("k_p2p_blocks");
+}
+void launch_direct(KSpec ks, int dim, const double* pts, long long N, const double* x,
+                   long long ldx, double* y, long long ldy, int nrhs, cudaStream_t s) {
+  const int blocks = (int)((N + 255) / 256);
+  Prof p("k_direct", 2.0 * (double)N * N * nrhs, 0.0, s);
+  for (int c = 0; c < nrhs; c++) {
+    k_direct<<<blocks, 256, 0, s>>>(ks, dim, pts, N, x, ldx, y, ldy, c);
+    CK_LAUNCH("k_direct");
+  }
+}
+void launch_gather_rows(const long long* perm, long long N, const double* in, long long ldi,
+                        double* out, long long ldo, int ncols, cudaStream_t s) {
+  if (N <= 0) return;
+  k_gather_rows<<<(int)((N + 255) / 256), 256, 0, s>>>(perm, N, in, ldi, out, ldo, ncols);
+  CK_LAUNCH("k_gather_rows");
+}
+void launch_scatter_rows(const long long* perm, long long N, const double* in, long long ldi,
+                         double* out, long long ldo, int ncols, cudaStream_t s) {
+  if (N <= 0) return;
+  k_scatter_rows<<<(int)((N + 255) / 256), 256, 0, s>>>(perm, N, in, ldi, out, ldo, ncols);
+  CK_LAUNCH("k_scatter_rows");
+}
+
+}  // namespace ifmm

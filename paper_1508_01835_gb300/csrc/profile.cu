@@ -1,0 +1,113 @@
+// profile.cu -- optional timing of the library's own launches.
+//
+// When enabled, every profiled launch is bracketed by two CUDA events on the
+// stream it is launched on, tagged with the kernel name and the algorithmic
+// flops and bytes of that launch.  Collection synchronises once and sums the
+// event intervals per kernel name.
+#include <mutex>
+
+#include "internal.cuh"
+
+namespace ifmm {
+
+unsigned long long& launch_counter() {
+  static unsigned long long n = 0;
+  return n;
+}
+
+namespace prof {
+
+struct Pending {
+  const char* name;
+  cudaEvent_t a, b;
+  double flops, bytes;
+};
+struct Stat {
+  long long launches = 0;
+  double seconds = 0.0, flops = 0.0, bytes = 0.0;
+};
+
+static std::mutex mu;
+static bool on = false;
+static std::vector<Pending> pending;
+static std::vector<cudaEvent_t> pool;
+static std::map<std::string, Stat> stats;
+static unsigned long long launches_at_start = 0;
+
+static cudaEvent_t get_event() {
+  if (!pool.empty()) {
+    cudaEvent_t e = pool.back();
+    pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  CK(cudaEventCreate(&e));
+  return e;
+}
+
+bool enabled() { return on; }
+
+void* begin(const char* name, double flops, double bytes, cudaStream_t s) {
+  if (!on) return nullptr;
+  std::lock_guard<std::mutex> g(mu);
+  Pending p{name, get_event(), get_event(), flops, bytes};
+  CK(cudaEventRecord(p.a, s));
+  pending.push_back(p);
+  return reinterpret_cast<void*>(pending.size());
+}
+
+void end(void* token, cudaStream_t s) {
+  if (!on || !token) return;
+  std::lock_guard<std::mutex> g(mu);
+  const size_t i = reinterpret_cast<size_t>(token) - 1;
+  CK(cudaEventRecord(pending[i].b, s));
+}
+
+static void drain() {
+  CK(cudaDeviceSynchronize());
+  for (Pending& p : pending) {
+    float ms = 0.0f;
+    CK(cudaEventElapsedTime(&ms, p.a, p.b));
+    Stat& st = stats[p.name];
+    st.launches++;
+    st.seconds += ms * 1e-3;
+    st.flops += p.flops;
+    st.bytes += p.bytes;
+    pool.push_back(p.a);
+    pool.push_back(p.b);
+  }
+  pending.clear();
+}
+
+void start() {
+  std::lock_guard<std::mutex> g(mu);
+  if (on) drain();
+  stats.clear();
+  launches_at_start = launch_counter();
+  on = true;
+}
+
+int stop(ifmm_kernel_stat* out, int capacity) {
+  std::lock_guard<std::mutex> g(mu);
+  drain();
+  on = false;
+  Stat& all = stats["(all launches)"];
+  all.launches = (long long)(launch_counter() - launches_at_start);
+  int n = 0;
+  for (auto& kv : stats) {
+    if (out && n < capacity) {
+      ifmm_kernel_stat& o = out[n];
+      std::memset(&o, 0, sizeof(o));
+      std::strncpy(o.name, kv.first.c_str(), sizeof(o.name) - 1);
+      o.launches = kv.second.launches;
+      o.seconds = kv.second.seconds;
+      o.flops = kv.second.flops;
+      o.bytes = kv.second.bytes;
+    }
+    n++;
+  }
+  return n;
+}
+
+}  // namespace prof
+}  // namespace ifmm

@@ -1,0 +1,150 @@
+// system.cuh -- the system object: tree topology, raw operators, product plans.
+#pragma once
+#include <algorithm>
+#include <limits>
+
+#include "kernels_ops.cuh"
+
+struct ifmm_ctx {
+  int device = 0;
+  std::string last_error;
+};
+
+namespace ifmm {
+
+void build_lists_device(const std::vector<std::vector<unsigned long long>>& keys, int dim,
+                        std::vector<std::vector<int>>& nbr, std::vector<std::vector<int>>& far,
+                        cudaStream_t s);
+void morton_decode_host(unsigned long long k, int dim, int* c);
+
+// One depth of the tree, boxes in Morton order.
+struct LevelTopo {
+  int l = 0, nb = 0;
+  double h = 0.0;                       // box half-width
+  std::vector<int> coords;              // nb x 3
+  std::vector<int> parent;              // index at depth l-1
+  std::vector<int> cb, ce;              // children range at depth l+1
+  std::vector<int> colour;
+  std::vector<int> nbr_ptr, nbr;        // N_i, sorted, includes i
+  std::vector<int> far_ptr, far;        // I_i, sorted
+  std::vector<int> yl_ptr, yl;          // N_i u I_i, sorted
+  std::vector<int> p0, p1;              // leaves: point range (tree order)
+  int find(const std::vector<int>& ptr, const std::vector<int>& v, int i, int j) const {
+    auto b = v.begin() + ptr[i], e = v.begin() + ptr[i + 1];
+    auto it = std::lower_bound(b, e, j);
+    return (it != e && *it == j) ? (int)(it - v.begin()) : -1;
+  }
+  int nslot(int i, int j) const { return find(nbr_ptr, nbr, i, j); }
+  int yslot(int i, int j) const { return find(yl_ptr, yl, i, j); }
+  bool is_nbr(int i, int j) const { return nslot(i, j) >= 0; }
+  int child_pos(int i, int dim) const {
+    int p = 0;
+    for (int d = 0; d < dim; d++) p |= (coords[i * 3 + d] & 1) << d;
+    return p;
+  }
+  int m2l_offset(int i, int q, int dim) const {
+    int o = 0, w = 1;
+    for (int d = 0; d < dim; d++) {
+      o += (coords[q * 3 + d] - coords[i * 3 + d] + 3) * w;
+      w *= 7;
+    }
+    return o;
+  }
+};
+
+// Chebyshev operators of one order n.
+struct ChebOps {
+  int n = 0, nd = 0;
+  ChebSpec spec{};
+  double* leafU = nullptr;          // per leaf m_i x nd (ld m_i)
+  std::vector<long long> uoff;
+  double* transfer = nullptr;       // 2^D blocks nd x nd
+  std::vector<double*> m2l;         // per depth: 7^D blocks nd x nd (depth >= 2)
+};
+
+// A launch sequence of block-row products.
+struct SpPhase {
+  SpRow* rows = nullptr;
+  SpEnt* ents = nullptr;
+  int nrows = 0;
+  double flops = 0.0, bytes = 0.0;  // per right-hand side
+};
+struct SpPlan {
+  std::vector<SpPhase> phases;
+  Arena mem;
+  void run(int nrhs, cudaStream_t s) const {
+    for (const SpPhase& p : phases)
+      launch_spmm(p.rows, p.nrows, p.ents, nrhs, s, p.flops, p.bytes * nrhs);
+  }
+};
+struct SpBuild {
+  std::vector<SpRow> rows;
+  std::vector<SpEnt> ents;
+  void row(double* y, long long ldy, int m, double beta = 0.0) {
+    rows.push_back({y, ldy, m, (int)ents.size(), 0, beta});
+  }
+  void ent(const double* A, int lda, int k, int transA, const double* x, long long ldx,
+           double alpha = 1.0) {
+    ents.push_back({A, x, ldx, lda, k, transA, alpha});
+    rows.back().ne++;
+  }
+  void flush(SpPlan& plan, cudaStream_t s, int nrhs = 1) {
+    if (rows.empty()) return;
+    validate_spmm(rows, ents, nrhs);
+    SpPhase ph;
+    for (const SpRow& R : rows) {
+      ph.bytes += 8.0 * R.m;
+      for (int e = R.e0; e < R.e0 + R.ne; e++) {
+        const SpEnt& E = ents[e];
+        ph.flops += 2.0 * R.m * (double)E.k;
+        ph.bytes += 8.0 * E.k + (E.A ? 8.0 * R.m * (double)E.k : 0.0);
+      }
+    }
+    ph.nrows = (int)rows.size();
+    ph.rows = upload(plan.mem, rows, s);
+    ph.ents = upload(plan.mem, ents, s);
+    plan.phases.push_back(ph);
+    rows.clear();
+    ents.clear();
+  }
+};
+
+}  // namespace ifmm
+
+struct ifmm_system {
+  ifmm_ctx* ctx = nullptr;
+  long long N = 0;
+  int dim = 3;
+  ifmm::KSpec ks{};
+  ifmm_options opt{};
+  int L = 0;
+  double lo[3] = {0, 0, 0};
+  double edge = 1.0;
+  int max_leaf = 0;
+  ifmm::Arena mem;                           // points, perm, operators, near field
+  double* pts_user = nullptr;
+  double* pts_tree = nullptr;
+  long long* perm = nullptr;
+  std::vector<long long> perm_h;
+  std::vector<ifmm::LevelTopo> lv;           // depths 0..L
+  double* p2p = nullptr;                     // near-field blocks
+  std::vector<long long> p2p_off;            // per leaf neighbour slot
+  ifmm::ChebOps ops_f, ops_mv;               // factor order / matvec order
+  bool same_ops = true;
+  // FMM matvec plan and its workspace (grown on demand)
+  ifmm::Arena fmm_ws;
+  ifmm::SpPlan fmm_plan;
+  int fmm_cap = 0;
+  double *fmm_x = nullptr, *fmm_y = nullptr;
+  double sigma0 = std::numeric_limits<double>::quiet_NaN();
+  int sigma0_iters = 0;
+  const ifmm::ChebOps& mv() const { return same_ops ? ops_f : ops_mv; }
+};
+
+namespace ifmm {
+ifmm_system* system_create(ifmm_ctx* ctx, const double* pts, bool host, long long N,
+                           const ifmm_kernel* k, const ifmm_options* opt, cudaStream_t s);
+void system_matvec(ifmm_system* sys, int mode, const double* x, long long ldx, double* y,
+                   long long ldy, int nrhs, cudaStream_t s);
+double system_sigma0(ifmm_system* sys, cudaStream_t s, int* iters);
+}  // namespace ifmm

@@ -11,3 +11,6 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU and the built C-ABI library")
     config.addinivalue_line("markers", "slow: long-running CPU oracle case")
+
+# GPU tests run the library with host-side bounds validation of every launch
+os.environ.setdefault("IFMM_VALIDATE", "1")

@@ -1,0 +1,57 @@
+"""The C-ABI library loads and exports every function include/ifmm.h declares
+(no GPU needed: nothing here launches a kernel)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ifmm.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b([a-z_][a-z0-9_]*)\s*\(", text,
+                       flags=re.M)
+    return sorted(set(n for n in names if not n.startswith("typedef")))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_1508_01835_gb300 as pkg
+    from paper_1508_01835_gb300 import build
+    build.build()
+    return pkg.lib()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("ifmm_factor", "ifmm_solve", "fmm_matvec", "gmres_solve", "ifmm_system_create",
+                 "ifmm_sigma0", "gmres_solve_host"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings_and_argument_checks(lib):
+    assert lib.ifmm_status_string(0) == b"ok"
+    assert lib.ifmm_status_string(4) == b"singular pivot block"
+    # NULL handles are rejected before any CUDA call
+    assert lib.ifmm_solve(None, None, None, None, 1, 10, None) == 1
+    assert lib.fmm_matvec(None, None, 0, None, None, 1, 10, None) == 1
+    assert lib.ifmm_factor(None, None, None, None) == 1
+    out = ctypes.c_void_p()
+    assert lib.ifmm_ctx_create(-1, ctypes.byref(out)) == 1
+
+
+def test_product_path_fails_loudly_without_library(tmp_path, monkeypatch):
+    import paper_1508_01835_gb300 as pkg
+    monkeypatch.setattr(pkg, "_lib", None)
+    monkeypatch.setattr(pkg, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError):
+        pkg.lib()

@@ -1,0 +1,233 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the CPU oracle.
+
+Every case builds the same seeded inputs on both sides.  Integer structure
+(tree order, box counts, ranks) must agree exactly; floating point within the
+tolerances stated per test (FP64 rounding differences only).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import paper_1508_01835_gb300 as ifmm
+from oracle.gmres import gmres as oracle_gmres
+from oracle.ifmm import IFMM, sigma0_power
+from tests.gpu_util import cuda, dense_an_solve, kernel, opts, oracle_h2, rel, to_user
+from workloads import Kernel, K_GAUSSIAN, K_INV_R, K_PAPER_D, c1, small_cube
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    "c1": lambda: c1(),                                                   # L = 2, n = 3
+    "3lev": lambda: small_cube(3000, 7, cheb_n=3, leaf_max=32, eps=1e-6),  # L = 3, one merge
+    "2d": lambda: small_cube(2500, 9, cheb_n=4, leaf_max=20, eps=1e-8, dim=2,
+                             kernel=Kernel(K_GAUSSIAN, 0.05, 1.01)),
+    "paper": lambda: small_cube(1800, 5, cheb_n=2, leaf_max=16, eps=1e-4,
+                                kernel=Kernel(K_PAPER_D, 0.05, 1.0)),
+    "ragged": lambda: small_cube(1001, 3, cheb_n=3, leaf_max=13, eps=1e-7),
+}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1508_01835_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+    c = ifmm.ifmm_ctx_create(0)
+    yield c
+    ifmm.ifmm_ctx_destroy(c)
+
+
+def make_sys(ctx, w, **kw):
+    return ifmm.ifmm_system_create(ctx, cuda(w.points), kernel(w), opts(w, **kw))
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_tree_matches_oracle(ctx, name):
+    w = CASES[name]()
+    h2 = oracle_h2(w)
+    sys = make_sys(ctx, w)
+    try:
+        info = ifmm.ifmm_system_get_info(sys)
+        assert info.levels == h2.tree.L
+        for l in range(h2.tree.L + 1):
+            assert info.boxes[l] == h2.tree.levels[l].nb
+        perm = ifmm.ifmm_system_get_perm(sys, w.N)
+        assert np.array_equal(perm, h2.tree.perm)
+    finally:
+        ifmm.ifmm_system_destroy(sys)
+
+
+@pytest.mark.parametrize("name", ["c1", "2d", "ragged", "3lev", "paper"])
+def test_matvec_parity(ctx, name):
+    w = CASES[name]()
+    h2 = oracle_h2(w)
+    sys = make_sys(ctx, w)
+    try:
+        X = np.random.default_rng(3).standard_normal((3, w.N))
+        x = cuda(X)
+        y = torch.empty_like(x)
+        ifmm.fmm_matvec(ctx, sys, ifmm.MV_FMM, x, y, w.N)
+        p = h2.tree.perm
+        ref = np.stack([to_user(h2, h2.matvec(X[c][p])) for c in range(3)])
+        assert rel(y.cpu().numpy(), ref) < 1e-13
+        ifmm.fmm_matvec(ctx, sys, ifmm.MV_DIRECT, x, y, w.N)
+        refd = np.stack([to_user(h2, h2.direct_matvec(X[c][p])) for c in range(3)])
+        assert rel(y.cpu().numpy(), refd) < 1e-13
+    finally:
+        ifmm.ifmm_system_destroy(sys)
+
+
+@pytest.mark.parametrize("name", ["c1", "3lev"])
+def test_sigma0_parity(ctx, name):
+    w = CASES[name]()
+    h2 = oracle_h2(w)
+    s_ref, it_ref = sigma0_power(h2)
+    sys = make_sys(ctx, w)
+    try:
+        s, it = ifmm.ifmm_sigma0(ctx, sys)
+        assert it == it_ref
+        assert abs(s - s_ref) <= 1e-10 * s_ref
+    finally:
+        ifmm.ifmm_system_destroy(sys)
+
+
+@pytest.mark.parametrize("N,n,leaf,dim,kern", [
+    (600, 3, 16, 3, None),
+    (1500, 2, 12, 3, Kernel(K_INV_R, 0.0, 3000.0)),
+    (900, 3, 10, 2, Kernel(K_GAUSSIAN, 0.15, 1.01)),
+])
+def test_tau_zero_is_exact(ctx, N, n, leaf, dim, kern):
+    """Compression disabled: the GPU factorisation is an exact block LU of E."""
+    w = small_cube(N, 21, cheb_n=n, leaf_max=leaf, dim=dim, kernel=kern)
+    h2 = oracle_h2(w)
+    b = np.random.default_rng(1).standard_normal(N)
+    x_ref, kappa = dense_an_solve(h2, b)
+    sys = make_sys(ctx, w, eps=0.0)
+    fac = ifmm.ifmm_factor(ctx, sys)
+    try:
+        x = torch.empty(N, dtype=torch.float64, device="cuda:0")
+        ifmm.ifmm_solve(ctx, fac, cuda(b), x, N)
+        assert rel(x.cpu().numpy(), x_ref) < 1e-14 * kappa * 50
+    finally:
+        ifmm.ifmm_factor_destroy(fac)
+        ifmm.ifmm_system_destroy(sys)
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_factor_solve_parity(ctx, name):
+    """Same tau on both sides: equal ranks, equal solve output to rounding."""
+    w = CASES[name]()
+    h2 = oracle_h2(w)
+    ora = IFMM(h2, w.eps)
+    sys = make_sys(ctx, w, tau=ora.tau, rank_cap=1 << 20)
+    fac = ifmm.ifmm_factor(ctx, sys)
+    try:
+        for l in range(2, h2.tree.L + 1):
+            g = ifmm.ifmm_factor_get_ranks(fac, l)
+            assert g == ora.ranks(l), f"ranks differ at depth {l}"
+        B = w.rhs(2).T.copy()
+        X = torch.empty(2, w.N, dtype=torch.float64, device="cuda:0")
+        ifmm.ifmm_solve(ctx, fac, cuda(B), X, w.N)
+        ref = ora.solve(B.T).T
+        assert rel(X.cpu().numpy(), ref) < 1e-10
+    finally:
+        ifmm.ifmm_factor_destroy(fac)
+        ifmm.ifmm_system_destroy(sys)
+
+
+def test_gmres_c1_direct_matches_dense_lu(ctx):
+    """C1: GMRES with the exact matvec and the IFMM preconditioner reaches
+    1e-10 and agrees with the dense LU solve of A (Sec. 3.2)."""
+    w = c1()
+    h2 = oracle_h2(w)
+    b = w.rhs(1)[:, 0]
+    A = h2.dense_exact()
+    p = h2.tree.perm
+    x_ref = to_user(h2, np.linalg.solve(A, b[p]))
+    kappa = np.linalg.cond(A)
+    sys = make_sys(ctx, w)
+    fac = ifmm.ifmm_factor(ctx, sys)
+    try:
+        x = torch.empty(w.N, dtype=torch.float64, device="cuda:0")
+        rep = ifmm.gmres_solve(ctx, sys, fac, ifmm.MV_DIRECT, cuda(b), x, w.N, 1e-10, 500)[0]
+        assert rep.status == 0 and rep.true_rel_residual <= 1e-10
+        assert rel(x.cpu().numpy(), x_ref) < max(1e-8, 1e-10 * kappa * 10)
+    finally:
+        ifmm.ifmm_factor_destroy(fac)
+        ifmm.ifmm_system_destroy(sys)
+
+
+@pytest.mark.parametrize("name", ["c1", "3lev"])
+def test_gmres_parity_with_oracle(ctx, name):
+    """FMM matvec + IFMM right preconditioner: same iteration count as the
+    oracle's GMRES (+-1), true residual <= 1e-10, same solution to 1e-8."""
+    w = CASES[name]()
+    h2 = oracle_h2(w)
+    ora = IFMM(h2, w.eps)
+    b = w.rhs(1)[:, 0]
+    p = h2.tree.perm
+
+    def mv(v):
+        return to_user(h2, h2.matvec(v[p]))
+
+    x_o, it_o, res_o = oracle_gmres(mv, b, ora.solve, 1e-10, 500)
+    sys = make_sys(ctx, w, tau=ora.tau, rank_cap=1 << 20)
+    fac = ifmm.ifmm_factor(ctx, sys)
+    try:
+        x = torch.empty(w.N, dtype=torch.float64, device="cuda:0")
+        rep = ifmm.gmres_solve(ctx, sys, fac, ifmm.MV_FMM, cuda(b), x, w.N, 1e-10, 500)[0]
+        assert rep.true_rel_residual <= 1e-10
+        assert abs(rep.iters - it_o) <= 1
+        assert rel(x.cpu().numpy(), x_o) < 1e-8
+    finally:
+        ifmm.ifmm_factor_destroy(fac)
+        ifmm.ifmm_system_destroy(sys)
+
+
+def test_multi_rhs_gmres_and_host_entry(ctx):
+    w = CASES["ragged"]()
+    sys = make_sys(ctx, w)
+    fac = ifmm.ifmm_factor(ctx, sys)
+    try:
+        B = w.rhs(3).T.copy()
+        X = torch.empty(3, w.N, dtype=torch.float64, device="cuda:0")
+        reps = ifmm.gmres_solve(ctx, sys, fac, ifmm.MV_FMM, cuda(B), X, w.N, 1e-10, 200)
+        assert all(r.status == 0 and r.true_rel_residual <= 1e-10 for r in reps)
+        Xh = np.zeros_like(B)
+        reps_h = ifmm.gmres_solve_host(ctx, sys, fac, ifmm.MV_FMM, B, Xh, 1e-10, 200)
+        assert [r.iters for r in reps_h] == [r.iters for r in reps]
+        assert rel(Xh, X.cpu().numpy()) < 1e-12
+    finally:
+        ifmm.ifmm_factor_destroy(fac)
+        ifmm.ifmm_system_destroy(sys)
+
+
+def test_dense_mode_small_n(ctx):
+    w = small_cube(50, 2, cheb_n=3, leaf_max=64)
+    h2 = oracle_h2(w)
+    sys = make_sys(ctx, w)
+    fac = ifmm.ifmm_factor(ctx, sys)
+    try:
+        assert ifmm.ifmm_system_get_info(sys).levels == 0
+        b = np.random.default_rng(0).standard_normal(50)
+        x = torch.empty(50, dtype=torch.float64, device="cuda:0")
+        ifmm.ifmm_solve(ctx, fac, cuda(b), x, 50)
+        assert rel(x.cpu().numpy(), np.linalg.solve(h2.dense_exact(), b)) < 1e-12
+    finally:
+        ifmm.ifmm_factor_destroy(fac)
+        ifmm.ifmm_system_destroy(sys)
+
+
+def test_invalid_arguments_are_rejected(ctx):
+    w = small_cube(100, 1)
+    pts = cuda(w.points)
+    with pytest.raises(ifmm.IFMMError) as e:
+        ifmm.ifmm_system_create(ctx, pts, kernel(w), opts(w, eps=-1.0))
+    assert e.value.status == 1
+    bad = ifmm.make_options(dim=4, cheb_n=3, leaf_max=16, eps=1e-6)
+    with pytest.raises(ifmm.IFMMError):
+        ifmm.ifmm_system_create(ctx, pts, kernel(w), bad)
+    with pytest.raises(ifmm.IFMMError):
+        ifmm.ifmm_system_create(ctx, pts, ifmm.Kernel(K_INV_R, 0.0, math.nan), opts(w))
