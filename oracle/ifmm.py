@@ -49,8 +49,14 @@ R7  parent bases are initialised after the children's level is eliminated
     (Algorithm 1 lists initialisation first; the parent's U, V depend on the
     children's r_j, t_j of Eqs. U_parent_j_update, V_parent_j_update).
 R8  pivoting: partial (row) pivoting inside E(P, P) only (LAPACK getrf).
-R9  an optional rank cap (default: none) bounds r; the CUDA path states its
-    cap and the tests run where it does not bind.
+R9  an optional rank cap bounds r (default here: none; the CUDA library's
+    default is n^D, the rank of the initial Chebyshev representation).
+R3b blocks taller than 144 rows that are truncated below their height are
+    recompressed with the randomised SVD of the paper's Sec. 2.4 (Halko et
+    al.): k = min(a, cap + 16, 144) columns of a uniform [-1, 1) test matrix
+    drawn from a counter-based SplitMix64 stream (seeded by level, box and
+    side, so the CUDA path draws the same numbers), one power iteration with
+    re-orthonormalisation, and the exact SVD of the projected k-row matrix.
 
 Parity: pinned by tests -- with tau = 0 the factorisation is an exact block
 LU of E and the solve equals the dense solve of A_n to rounding; the
@@ -114,6 +120,54 @@ def left_svd(M: np.ndarray):
     return W, s
 
 
+SVD_EXACT_MAX_A = 144
+RSVD_OVERSAMPLE = 16
+_M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+
+def splitmix64(x):
+    """SplitMix64 finaliser on uint64 arrays (wrapping arithmetic)."""
+    x = np.asarray(x, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        x = x + np.uint64(0x9E3779B97F4A7C15)
+        x = (x ^ (x >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        x = (x ^ (x >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+    return x ^ (x >> np.uint64(31))
+
+
+def rsvd_seed(level: int, box: int, side: int) -> np.uint64:
+    v = (np.uint64(level) << np.uint64(40)) ^ (np.uint64(box) << np.uint64(2)) ^ np.uint64(side)
+    return splitmix64(v)
+
+
+def uniform_test_matrix(rows: int, cols: int, seed) -> np.ndarray:
+    """Omega[i, c] = 2 u - 1, u = (splitmix64(seed + i + c rows) >> 11) 2^-53."""
+    e = np.arange(rows * cols, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        x = splitmix64(np.uint64(seed) + e)
+    u = (x >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    return (2.0 * u - 1.0).reshape(cols, rows).T
+
+
+def orth(X: np.ndarray) -> np.ndarray:
+    """Orthonormal basis of range(X) from the SVD of X^T; directions with
+    sigma <= 1e-10 sigma_max are numerically null and dropped (zero columns)."""
+    W, s = left_svd(X.T)
+    inv = np.where((s > 1e-10 * s[0]) & (s > 0), 1.0 / np.where(s > 0, s, 1.0), 0.0) if s.size else s
+    return X @ (W * inv[None, :])
+
+
+def rsvd_left(M: np.ndarray, k: int, seed) -> tuple[np.ndarray, np.ndarray]:
+    """Randomised top-k left singular vectors and values of M (reading R3b)."""
+    a, w = M.shape
+    Om = uniform_test_matrix(w, k, seed)
+    Q = orth(M @ Om)
+    Qz = orth(M.T @ Q)
+    Q = orth(M @ Qz)
+    Wb, s = left_svd(Q.T @ M)
+    return Q @ Wb, s
+
+
 def count_rank(s: np.ndarray, tau: float, full: int) -> int:
     if tau <= 0.0:
         return full
@@ -159,8 +213,9 @@ class IFMM:
     """Plain IFMM factorisation of the H^2 matrix A_n defined by ``h2``."""
 
     def __init__(self, h2: H2, eps: float, tau: float | None = None, rank_cap: int | None = None,
-                 sigma0: float | None = None):
+                 sigma0: float | None = None, rsvd_rows: int = SVD_EXACT_MAX_A):
         self.h2 = h2
+        self.rsvd_rows = rsvd_rows
         self.tree = h2.tree
         self.eps = eps
         self.rank_cap = rank_cap
@@ -314,9 +369,17 @@ class IFMM:
             MU = np.hstack([st.U[j] * st.SU[j][None, :]] + FU)
             MV = np.hstack([st.V[j] * st.SV[j][None, :]] + FV)
             aj = st.a[j]
-            WU, sU = left_svd(MU)
-            WV, sV = left_svd(MV)
-            rn = min(max(count_rank(sU, self.tau, aj), count_rank(sV, self.tau, aj)), aj)
+            rcap = self._cap(aj)
+            if self.tau > 0 and aj > self.rsvd_rows and rcap < aj:
+                k = min(aj, rcap + RSVD_OVERSAMPLE, SVD_EXACT_MAX_A)
+                WU, sU = rsvd_left(MU, k, rsvd_seed(st.l, j, 0))
+                WV, sV = rsvd_left(MV, k, rsvd_seed(st.l, j, 1))
+                full = k
+            else:
+                WU, sU = left_svd(MU)
+                WV, sV = left_svd(MV)
+                full = aj
+            rn = min(max(count_rank(sU, self.tau, full), count_rank(sV, self.tau, full)), full)
             rn = self._cap(rn)
             Un, Vn = WU[:, :rn], WV[:, :rn]
             new[j] = (Un, Vn, sU[:rn].copy(), sV[:rn].copy(), Un.T @ st.U[j], Vn.T @ st.V[j])

@@ -34,7 +34,7 @@ class Kernel(C.Structure):
 class Options(C.Structure):
     _fields_ = [("dim", C.c_int), ("cheb_n", C.c_int), ("leaf_max", C.c_int), ("eps", C.c_double),
                 ("schur", C.c_int), ("tau_override", C.c_double), ("rank_cap", C.c_int),
-                ("fmm_n", C.c_int)]
+                ("fmm_n", C.c_int), ("rsvd_rows", C.c_int)]
 
 
 class GmresReport(C.Structure):
@@ -159,8 +159,8 @@ def ifmm_ctx_destroy(ctx):
 
 
 def make_options(dim=3, cheb_n=3, leaf_max=64, eps=1e-6, schur=P_FP64, tau_override=0.0,
-                 rank_cap=0, fmm_n=0) -> Options:
-    return Options(dim, cheb_n, leaf_max, eps, schur, tau_override, rank_cap, fmm_n)
+                 rank_cap=0, fmm_n=0, rsvd_rows=0) -> Options:
+    return Options(dim, cheb_n, leaf_max, eps, schur, tau_override, rank_cap, fmm_n, rsvd_rows)
 
 
 def ifmm_system_create(ctx, pts, kernel: Kernel, opt: Options, stream=None):

@@ -15,6 +15,7 @@
 //   4. merges the level into its parent (Eqs. y_merge - K_merge).
 // The top system for y^(2) is factorised densely.
 #include <chrono>
+#include <cstdio>
 #include <memory>
 #include <map>
 #include <set>
@@ -27,6 +28,21 @@ using Clock = std::chrono::steady_clock;
 static double since(Clock::time_point t) {
   return std::chrono::duration<double>(Clock::now() - t).count();
 }
+// IFMM_TRACE=1: one line per phase on stderr (sizes, ranks, seconds)
+static bool tracing() {
+  static const bool v = [] {
+    const char* e = std::getenv("IFMM_TRACE");
+    return e && e[0] == '1';
+  }();
+  return v;
+}
+#define TRACE(...) \
+  do {                                  \
+    if (tracing()) {                    \
+      std::fprintf(stderr, __VA_ARGS__); \
+      std::fflush(stderr);              \
+    }                                   \
+  } while (0)
 
 static inline GemmTask gm(const double* A, int lda, int tA, const double* B, int ldb, int tB,
                           double* C, int ldc, int M, int N, int K, double alpha, double beta) {
@@ -66,6 +82,18 @@ struct FLevel {
   std::vector<double*> Uraw, Vraw;  // raw bases of this level (a_i x nd, ld a_i)
   Arena mem;
 };
+
+// Tall blocks are recompressed with the randomised SVD when the rank cap is
+// below the block height and truncation is on (tau > 0): the top
+// k = min(a, cap + oversampling, 144) singular triplets decide the rank.
+static double g_tau_for_rsvd = 0.0;
+static int g_rsvd_rows = SVD_EXACT_MAX_A;
+static bool use_rsvd(int a, int rcap) {
+  return g_tau_for_rsvd > 0.0 && a > g_rsvd_rows && rcap < a;
+}
+static int rsvd_k(int a, int rcap) {
+  return std::min(std::min(a, rcap + RSVD_OVERSAMPLE), SVD_EXACT_MAX_A);
+}
 
 struct Factorizer {
   ifmm_system* sys;
@@ -151,21 +179,92 @@ struct Factorizer {
 
   // -------------------------------------------------------------------------
   // weighted initial bases of a level (footnote to Eq. U_j_recomp, reading R6)
+  //
+  // Small boxes (a <= n^D): left SVD of M = U_i [K_iq V_q^T]_{q in I_i}
+  // (a x sum a_q).  Tall boxes (a > n^D): the same subspace from the reduced
+  // form C = R_i [K_iq R_q^T]_q (n^D x n^D |I_i|), where U_i = Q_i R_i comes
+  // from the SVD of U_i (R_i = Sigma_i W_i^T) and likewise R_q for V_q; then
+  // U_hat = U_i W_i Sigma_i^-1 W_C and r_i = W_C^T R_i.
   // -------------------------------------------------------------------------
+  struct Side {
+    std::vector<double*> W, sg;      // small boxes: W (a x a), sigma (a); tall: W_C, sigma_C (nd)
+    std::vector<double*> R, T2;      // all boxes: R (nd x nd); tall boxes: T2 = W Sigma^-1 W_C
+  };
+
+  // R_i (nd x nd) = diag(sigma) W^T from the SVD of raw^T (nd x a), for every box;
+  // T_i = W diag(1/sigma) (nd x nd) for the tall boxes
+  void raw_factors(FLevel& st, const std::vector<double*>& raw, std::vector<double*>& R,
+                   std::vector<double*>& Winv, Arena& keep) {
+    const int nb = st.nb;
+    std::vector<CopyTask> tr, sc;
+    std::vector<SvdTask> sv;
+    std::vector<double*> XT(nb), W(nb), sg(nb), P(nb);
+    R.assign(nb, nullptr);
+    Winv.assign(nb, nullptr);
+    for (int i = 0; i < nb; i++) {
+      const int a = st.a[i];
+      XT[i] = scratch.alloc<double>((size_t)nd * std::max(a, 1));
+      W[i] = scratch.alloc<double>((size_t)nd * nd);
+      sg[i] = keep.alloc<double>(nd);
+      P[i] = scratch.alloc<double>((size_t)nd * nd);
+      R[i] = keep.alloc<double>((size_t)nd * nd);
+      tr.push_back(cp(raw[i], a, XT[i], nd, nd, a, 1));
+      sv.push_back({XT[i], nd, nd, a, W[i], sg[i], nullptr});
+    }
+    run_copies(scratch, tr, s);
+    run_svd_left(scratch, sv, s);
+    std::vector<CopyTask> c2;
+    for (int i = 0; i < nb; i++) {
+      c2.push_back(cp(W[i], nd, P[i], nd, nd, nd, 0, 1.0, 0.0, sg[i]));  // W diag(sigma)
+    }
+    run_copies(scratch, c2, s);
+    c2.clear();
+    for (int i = 0; i < nb; i++) c2.push_back(cp(P[i], nd, R[i], nd, nd, nd, 1));  // R = (W S)^T
+    run_copies(scratch, c2, s);
+    // inverse sigma (dropping null directions) for the tall boxes
+    c2.clear();
+    std::vector<int> tall;
+    for (int i = 0; i < nb; i++)
+      if (st.a[i] > nd) tall.push_back(i);
+    if (!tall.empty()) {
+      std::vector<double*> inv(nb, nullptr);
+      std::vector<InvSigma> iv;
+      for (int i : tall) {
+        inv[i] = scratch.alloc<double>(nd);
+        Winv[i] = keep.alloc<double>((size_t)nd * nd);
+        iv.push_back({sg[i], inv[i], nd});
+      }
+      run_inv_sigma(scratch, iv, s);
+      for (int i : tall) c2.push_back(cp(W[i], nd, Winv[i], nd, nd, nd, 0, 1.0, 0.0, inv[i]));
+      run_copies(scratch, c2, s);
+    }
+  }
+
   void init_basis(FLevel& st, const LevelTopo& lv) {
     const int nb = st.nb;
     const double s0 = std::isnan(sys->sigma0) ? 1.0 : sys->sigma0;
-    // process boxes in batches that keep the SVD inputs below ~2 GiB
+    Arena keep;  // per-box factors until ranks are known
+    scratch.reset();
+    std::vector<double*> RU, RV, TU, TV;
+    bool any_tall = false;
+    for (int i = 0; i < nb; i++) any_tall |= st.a[i] > nd;
+    if (any_tall) {
+      raw_factors(st, st.Uraw, RU, TU, keep);
+      raw_factors(st, st.Vraw, RV, TV, keep);
+    }
     std::vector<double*> WU(nb), WV(nb), sU(nb), sV(nb);
-    Arena keep;  // W and sigma of all boxes until ranks are known
+    std::vector<int> full(nb);
     for (int i = 0; i < nb; i++) {
       const int a = st.a[i];
-      WU[i] = keep.alloc<double>((size_t)a * a);
-      WV[i] = keep.alloc<double>((size_t)a * a);
-      sU[i] = keep.alloc<double>(a);
-      sV[i] = keep.alloc<double>(a);
+      const int dimW = a > nd ? nd : a;  // rows of the matrix whose SVD decides the rank
+      WU[i] = keep.alloc<double>((size_t)dimW * dimW);
+      WV[i] = keep.alloc<double>((size_t)dimW * dimW);
+      sU[i] = keep.alloc<double>(dimW);
+      sV[i] = keep.alloc<double>(dimW);
+      full[i] = std::min(a, nd);
     }
     int* d_r = keep.alloc<int>(nb);
+    CK(cudaStreamSynchronize(s));
     int i0 = 0;
     while (i0 < nb) {
       scratch.reset();
@@ -173,9 +272,10 @@ struct Factorizer {
       int i1 = i0;
       while (i1 < nb) {
         long long w = 0;
-        for (int k = lv.far_ptr[i1]; k < lv.far_ptr[i1 + 1]; k++) w += st.a[lv.far[k]];
+        for (int k = lv.far_ptr[i1]; k < lv.far_ptr[i1 + 1]; k++)
+          w += st.a[i1] > nd ? nd : st.a[lv.far[k]];
         if (w == 0) w = nd;
-        const long long need = 2 * ((long long)st.a[i1] * w + (long long)nd * w);
+        const long long need = 2 * ((long long)std::min(st.a[i1], nd) * w + (long long)nd * w);
         if (i1 > i0 && budget + need > (256ll << 20)) break;
         budget += need;
         i1++;
@@ -185,53 +285,67 @@ struct Factorizer {
       std::vector<SvdTask> svd;
       for (int i = i0; i < i1; i++) {
         const int a = st.a[i];
+        const bool tall = a > nd;
+        const int rows = tall ? nd : a;
         long long w = 0;
-        for (int k = lv.far_ptr[i]; k < lv.far_ptr[i + 1]; k++) w += st.a[lv.far[k]];
-        double* MU;
-        double* MV;
+        for (int k = lv.far_ptr[i]; k < lv.far_ptr[i + 1]; k++) w += tall ? nd : st.a[lv.far[k]];
+        double *MU, *MV;
         int wcols;
         if (w == 0) {
           // empty interaction list: weight the raw basis by sigma_0 (reading R6)
           wcols = nd;
-          MU = scratch.alloc<double>((size_t)a * nd);
-          MV = scratch.alloc<double>((size_t)a * nd);
-          cps.push_back(cp(st.Uraw[i], a, MU, a, a, nd, 0, s0));
-          cps.push_back(cp(st.Vraw[i], a, MV, a, a, nd, 0, s0));
+          MU = scratch.alloc<double>((size_t)rows * nd);
+          MV = scratch.alloc<double>((size_t)rows * nd);
+          if (tall) {
+            cps.push_back(cp(RU[i], nd, MU, nd, nd, nd, 0, s0));
+            cps.push_back(cp(RV[i], nd, MV, nd, nd, nd, 0, s0));
+          } else {
+            cps.push_back(cp(st.Uraw[i], a, MU, a, a, nd, 0, s0));
+            cps.push_back(cp(st.Vraw[i], a, MV, a, a, nd, 0, s0));
+          }
         } else {
           wcols = (int)w;
           double* BU = scratch.alloc<double>((size_t)nd * w);
           double* BV = scratch.alloc<double>((size_t)nd * w);
-          MU = scratch.alloc<double>((size_t)a * w);
-          MV = scratch.alloc<double>((size_t)a * w);
+          MU = scratch.alloc<double>((size_t)rows * w);
+          MV = scratch.alloc<double>((size_t)rows * w);
           long long off = 0;
           for (int k = lv.far_ptr[i]; k < lv.far_ptr[i + 1]; k++) {
             const int q = lv.far[k];
             const int aq = st.a[q];
             const double* Kiq = ops.m2l[lv.l] + (size_t)lv.m2l_offset(i, q, dim) * nd * nd;
             const double* Kqi = ops.m2l[lv.l] + (size_t)lv.m2l_offset(q, i, dim) * nd * nd;
-            // BU[:, off] = K_iq V_q^T ; BV[:, off] = K_qi^T U_q^T
-            g1.push_back(gm(Kiq, nd, 0, st.Vraw[q], aq, 1, BU + off * nd, nd, nd, aq, nd, 1.0, 0.0));
-            g1.push_back(gm(Kqi, nd, 1, st.Uraw[q], aq, 1, BV + off * nd, nd, nd, aq, nd, 1.0, 0.0));
-            off += aq;
+            if (tall) {
+              // BU[:, off] = K_iq R_q^T ; BV[:, off] = K_qi^T R_q(U)^T   (nd x nd)
+              g1.push_back(gm(Kiq, nd, 0, RV[q], nd, 1, BU + off * nd, nd, nd, nd, nd, 1.0, 0.0));
+              g1.push_back(gm(Kqi, nd, 1, RU[q], nd, 1, BV + off * nd, nd, nd, nd, nd, 1.0, 0.0));
+              off += nd;
+            } else {
+              // BU[:, off] = K_iq V_q^T ; BV[:, off] = K_qi^T U_q^T
+              g1.push_back(gm(Kiq, nd, 0, st.Vraw[q], aq, 1, BU + off * nd, nd, nd, aq, nd, 1.0, 0.0));
+              g1.push_back(gm(Kqi, nd, 1, st.Uraw[q], aq, 1, BV + off * nd, nd, nd, aq, nd, 1.0, 0.0));
+              off += aq;
+            }
           }
-          g2.push_back(gm(st.Uraw[i], a, 0, BU, nd, 0, MU, a, a, (int)w, nd, 1.0, 0.0));
-          g2.push_back(gm(st.Vraw[i], a, 0, BV, nd, 0, MV, a, a, (int)w, nd, 1.0, 0.0));
+          if (tall) {
+            g2.push_back(gm(RU[i], nd, 0, BU, nd, 0, MU, nd, nd, (int)w, nd, 1.0, 0.0));
+            g2.push_back(gm(RV[i], nd, 0, BV, nd, 0, MV, nd, nd, (int)w, nd, 1.0, 0.0));
+          } else {
+            g2.push_back(gm(st.Uraw[i], a, 0, BU, nd, 0, MU, a, a, (int)w, nd, 1.0, 0.0));
+            g2.push_back(gm(st.Vraw[i], a, 0, BV, nd, 0, MV, a, a, (int)w, nd, 1.0, 0.0));
+          }
         }
-        double* wk1 = a > 128 ? scratch.alloc<double>((size_t)a * a + (size_t)a * 32) : nullptr;
-        double* wk2 = a > 128 ? scratch.alloc<double>((size_t)a * a + (size_t)a * 32) : nullptr;
-        svd.push_back({MU, a, a, wcols, WU[i], sU[i], wk1});
-        svd.push_back({MV, a, a, wcols, WV[i], sV[i], wk2});
-        f->info.flops_lowrank += 4.0 * a * a * (double)wcols * 2;
+        svd.push_back({MU, rows, rows, wcols, WU[i], sU[i], nullptr});
+        svd.push_back({MV, rows, rows, wcols, WV[i], sV[i], nullptr});
+        f->info.flops_lowrank += 4.0 * rows * (double)rows * wcols;
       }
       run_copies(scratch, cps, s);
       run_gemms(scratch, g1, s);
       run_gemms(scratch, g2, s);
       run_svd_left(scratch, svd, s);
       std::vector<RankTask> rt;
-      for (int i = i0; i < i1; i++) {
-        const int k = std::min(st.a[i], nd);
-        rt.push_back({sU[i], sV[i], k, std::min(k, st.rcap[i]), d_r + i, d_counters});
-      }
+      for (int i = i0; i < i1; i++)
+        rt.push_back({sU[i], sV[i], full[i], std::min(full[i], st.rcap[i]), d_r + i, d_counters});
       const RankTask* drt = upload(scratch, rt, s);
       launch_rank(drt, (int)rt.size(), tau, s);
       CK(cudaStreamSynchronize(s));
@@ -239,25 +353,39 @@ struct Factorizer {
     }
     std::vector<int> r = read_ints(d_r, nb);
     scratch.reset();
-    // r_i = W_r^T U_raw, t_i = W_r^T V_raw; new bases; M2L edges; parent transfers
+    // new bases U_hat, V_hat (a x r) and the transforms r_i, t_i (r x nd)
     std::vector<double*> rt(nb), tt(nb);
     std::vector<GemmTask> g, g2;
     std::vector<CopyTask> cps;
     for (int i = 0; i < nb; i++) {
       const int a = st.a[i];
       st.r[i] = r[i];
-      rt[i] = scratch.alloc<double>((size_t)std::max(r[i], 1) * nd);
-      tt[i] = scratch.alloc<double>((size_t)std::max(r[i], 1) * nd);
-      g.push_back(gm(WU[i], a, 1, st.Uraw[i], a, 0, rt[i], std::max(r[i], 1), r[i], nd, a, 1.0, 0.0));
-      g.push_back(gm(WV[i], a, 1, st.Vraw[i], a, 0, tt[i], std::max(r[i], 1), r[i], nd, a, 1.0, 0.0));
-      cps.push_back(cp(WU[i], a, st.U[i], a, a, r[i]));
-      cps.push_back(cp(WV[i], a, st.V[i], a, a, r[i]));
+      const int ldr = std::max(r[i], 1);
+      rt[i] = scratch.alloc<double>((size_t)ldr * nd);
+      tt[i] = scratch.alloc<double>((size_t)ldr * nd);
+      if (a > nd) {
+        double* T2U = scratch.alloc<double>((size_t)nd * nd);
+        double* T2V = scratch.alloc<double>((size_t)nd * nd);
+        g.push_back(gm(TU[i], nd, 0, WU[i], nd, 0, T2U, nd, nd, r[i], nd, 1.0, 0.0));
+        g.push_back(gm(TV[i], nd, 0, WV[i], nd, 0, T2V, nd, nd, r[i], nd, 1.0, 0.0));
+        g2.push_back(gm(st.Uraw[i], a, 0, T2U, nd, 0, st.U[i], a, a, r[i], nd, 1.0, 0.0));
+        g2.push_back(gm(st.Vraw[i], a, 0, T2V, nd, 0, st.V[i], a, a, r[i], nd, 1.0, 0.0));
+        g.push_back(gm(WU[i], nd, 1, RU[i], nd, 0, rt[i], ldr, r[i], nd, nd, 1.0, 0.0));
+        g.push_back(gm(WV[i], nd, 1, RV[i], nd, 0, tt[i], ldr, r[i], nd, nd, 1.0, 0.0));
+      } else {
+        g.push_back(gm(WU[i], a, 1, st.Uraw[i], a, 0, rt[i], ldr, r[i], nd, a, 1.0, 0.0));
+        g.push_back(gm(WV[i], a, 1, st.Vraw[i], a, 0, tt[i], ldr, r[i], nd, a, 1.0, 0.0));
+        cps.push_back(cp(WU[i], a, st.U[i], a, a, r[i]));
+        cps.push_back(cp(WV[i], a, st.V[i], a, a, r[i]));
+      }
       cps.push_back(cp(sU[i], 1, st.SU[i], 1, r[i], 1));
       cps.push_back(cp(sV[i], 1, st.SV[i], 1, r[i], 1));
     }
     run_gemms(scratch, g, s);
+    run_gemms(scratch, g2, s);
     run_copies(scratch, cps, s);
     g.clear();
+    g2.clear();
     for (int i = 0; i < nb; i++) {
       const int ri = st.r[i];
       const int ldr = std::max(ri, 1);
@@ -406,18 +534,20 @@ struct Factorizer {
       if (cb.kind == 'x') wV[slot[cb.box]] += rb.dim;
     }
     std::vector<double*> MU(nJ), MV(nJ), WU(nJ), WV(nJ), sU(nJ), sV(nJ);
-    std::vector<int> cU(nJ), cV(nJ);
+    std::vector<int> cU(nJ), cV(nJ), kk(nJ);
     std::vector<CopyTask> cps;
     std::vector<SvdTask> svd;
+    std::vector<RsvdTask> rsvd;
     int* d_r = scratch.alloc<int>(nJ);
     for (int t = 0; t < nJ; t++) {
       const int j = J[t], a = st.a[j], r = st.r[j];
+      kk[t] = use_rsvd(a, st.rcap[j]) ? rsvd_k(a, st.rcap[j]) : a;  // singular values kept
       MU[t] = scratch.alloc<double>((size_t)a * wU[t]);
       MV[t] = scratch.alloc<double>((size_t)a * wV[t]);
-      WU[t] = scratch.alloc<double>((size_t)a * a);
-      WV[t] = scratch.alloc<double>((size_t)a * a);
-      sU[t] = scratch.alloc<double>(a);
-      sV[t] = scratch.alloc<double>(a);
+      WU[t] = scratch.alloc<double>((size_t)a * kk[t]);
+      WV[t] = scratch.alloc<double>((size_t)a * kk[t]);
+      sU[t] = scratch.alloc<double>(kk[t]);
+      sV[t] = scratch.alloc<double>(kk[t]);
       cps.push_back(cp(st.U[j], a, MU[t], a, a, r, 0, 1.0, 0.0, st.SU[j]));
       cps.push_back(cp(st.V[j], a, MV[t], a, a, r, 0, 1.0, 0.0, st.SV[j]));
       cU[t] = cV[t] = r;
@@ -442,15 +572,25 @@ struct Factorizer {
     run_copies(scratch, cps, s);
     std::vector<RankTask> rt;
     for (int t = 0; t < nJ; t++) {
-      const int a = st.a[J[t]];
-      double* wk1 = a > 128 ? scratch.alloc<double>((size_t)a * a + (size_t)a * 32) : nullptr;
-      double* wk2 = a > 128 ? scratch.alloc<double>((size_t)a * a + (size_t)a * 32) : nullptr;
-      svd.push_back({MU[t], a, a, wU[t], WU[t], sU[t], wk1});
-      svd.push_back({MV[t], a, a, wV[t], WV[t], sV[t], wk2});
-      rt.push_back({sU[t], sV[t], a, st.rcap[J[t]], d_r + t, d_counters});
-      f->info.flops_lowrank += 4.0 * a * (double)a * (wU[t] + wV[t]);
+      const int j = J[t], a = st.a[j];
+      if (kk[t] < a) {
+        rsvd.push_back({MU[t], a, a, wU[t], kk[t], rsvd_seed(lv.l, j, 0), WU[t], sU[t]});
+        rsvd.push_back({MV[t], a, a, wV[t], kk[t], rsvd_seed(lv.l, j, 1), WV[t], sV[t]});
+        f->info.flops_lowrank += 8.0 * a * (double)kk[t] * (wU[t] + wV[t]);
+      } else {
+        double* wk1 = a > 144 ? scratch.alloc<double>((size_t)a * a + (size_t)a * 32) : nullptr;
+        double* wk2 = a > 144 ? scratch.alloc<double>((size_t)a * a + (size_t)a * 32) : nullptr;
+        svd.push_back({MU[t], a, a, wU[t], WU[t], sU[t], wk1});
+        svd.push_back({MV[t], a, a, wV[t], WV[t], sV[t], wk2});
+        f->info.flops_lowrank += 4.0 * a * (double)a * (wU[t] + wV[t]);
+      }
+      rt.push_back({sU[t], sV[t], kk[t], st.rcap[j], d_r + t, d_counters});
     }
     run_svd_left(scratch, svd, s);
+    // randomised tasks, grouped by their common k
+    std::map<int, std::vector<RsvdTask>> byk;
+    for (auto& T : rsvd) byk[T.k].push_back(T);
+    for (auto& kv : byk) run_rsvd_left(scratch, kv.second, s);
     const RankTask* drt = upload(scratch, rt, s);
     launch_rank(drt, nJ, tau, s);
     std::vector<int> rn = read_ints(d_r, nJ);
@@ -642,12 +782,16 @@ struct Factorizer {
       auto ts = Clock::now();
       if (std::isnan(sys->sigma0)) sys->sigma0 = system_sigma0(sys, s, &sys->sigma0_iters);
       f->info.seconds_sigma0 = since(ts);
+      TRACE("[ifmm] sigma0 = %.6g (%d iterations), %.3f s\n", sys->sigma0, sys->sigma0_iters,
+            f->info.seconds_sigma0);
       tau = o.eps * sys->sigma0;
     }
     f->info.sigma0 = sys->sigma0;
     f->info.sigma0_iters = sys->sigma0_iters;
     f->info.tau = tau;
-    cap_global = o.rank_cap > 0 ? o.rank_cap : (tau == 0.0 ? (1 << 30) : 2 * nd);
+    g_tau_for_rsvd = tau;
+    g_rsvd_rows = o.rsvd_rows > 0 ? o.rsvd_rows : SVD_EXACT_MAX_A;
+    cap_global = o.rank_cap > 0 ? o.rank_cap : (tau == 0.0 ? (1 << 30) : nd);
     f->rank.assign(L + 1, {});
     f->yoff.assign(L + 1, {});
     auto st = std::make_unique<FLevel>();
@@ -672,6 +816,13 @@ struct Factorizer {
       auto ti = Clock::now();
       init_basis(*st, lv);
       f->info.seconds_init += since(ti);
+      if (tracing()) {
+        int amax = 0, rmax = 0;
+        double rs = 0;
+        for (int i = 0; i < lv.nb; i++) { amax = std::max(amax, st->a[i]); rmax = std::max(rmax, st->r[i]); rs += st->r[i]; }
+        TRACE("[ifmm] level %d init: %d boxes, max a %d, max r %d, avg r %.1f, %.3f s\n", l, lv.nb,
+              amax, rmax, rs / std::max(lv.nb, 1), since(ti));
+      }
       auto te = Clock::now();
       int ncol = 1;
       for (int d = 0; d < dim; d++) ncol *= 3;
@@ -679,7 +830,16 @@ struct Factorizer {
         std::vector<int> boxes;
         for (int i = 0; i < lv.nb; i++)
           if (lv.colour[i] == c) boxes.push_back(i);
-        if (!boxes.empty()) eliminate_colour(*st, lv, boxes);
+        if (boxes.empty()) continue;
+        auto tc = Clock::now();
+        eliminate_colour(*st, lv, boxes);
+        if (tracing()) {
+          CK(cudaStreamSynchronize(s));
+          int amax = 0, rmax = 0;
+          for (int i : boxes) { amax = std::max(amax, st->a[i]); rmax = std::max(rmax, st->r[i]); }
+          TRACE("[ifmm] level %d colour %2d: %4zu boxes, max a %d, max r %d, %.3f s\n", l, c,
+                boxes.size(), amax, rmax, since(tc));
+        }
       }
       CK(cudaStreamSynchronize(s));
       f->info.seconds_elim += since(te);
@@ -699,11 +859,13 @@ struct Factorizer {
         merge(*st, lv, *nst, sys->lv[l - 1]);
         st = std::move(nst);
         f->info.seconds_elim += since(tm);
+        TRACE("[ifmm] merge %d -> %d: %.3f s\n", l, l - 1, since(tm));
       }
     }
     auto tt = Clock::now();
     top(*st, sys->lv[2]);
     f->info.seconds_top = since(tt);
+    TRACE("[ifmm] top: n = %d, %.3f s\n", f->top_n, f->info.seconds_top);
     std::vector<int> cnt = read_ints(d_counters, 4);
     f->info.rank_capped = cnt[0];
   }

@@ -269,6 +269,27 @@ struct SvdTask {
 };
 void run_svd_left(Arena& ar, const std::vector<SvdTask>& tasks, cudaStream_t s);
 
+// Randomised left SVD for blocks with a > 144 rows: top k left singular
+// vectors W (a x k, ld a) and values sigma (k); every task of a call has the same k.
+struct RsvdTask {
+  const double* M;
+  int ldm, a, w, k;
+  unsigned long long seed;
+  double* W;
+  double* sigma;
+};
+void run_rsvd_left(Arena& ar, const std::vector<RsvdTask>& tasks, cudaStream_t s);
+constexpr int SVD_EXACT_MAX_A = 144;  // larger blocks use run_rsvd_left when truncating
+constexpr int RSVD_OVERSAMPLE = 16;
+unsigned long long rsvd_seed(int level, int box, int side);
+// inv[c] = 1 / s[c] where s[c] > 1e-10 s[0], else 0
+struct InvSigma {
+  const double* s;
+  double* inv;
+  int k;
+};
+void run_inv_sigma(Arena& ar, const std::vector<InvSigma>& v, cudaStream_t s);
+
 // r_out[j] = min(max(#(sigU > tau), #(sigV > tau)), full, cap) (tau <= 0: full)
 struct RankTask {
   const double* sigU;

@@ -486,8 +486,8 @@ void run_getrs(Arena& ar, const std::vector<RsTask>& tasks, cudaStream_t s) {
 // structure of M.  Both phases live in shared memory when a <= SVD_SMEM_A,
 // otherwise in the task's global scratch.
 // ---------------------------------------------------------------------------
-constexpr int SVD_SMEM_A = 128;
-constexpr int SVD_CW = 32;
+constexpr int SVD_SMEM_A = 144;
+constexpr int SVD_CW = 16;
 
 struct SvdView {
   double* L;    // a x a, ld = lda
@@ -696,6 +696,144 @@ void run_svd_left(Arena& ar, const std::vector<SvdTask>& tasks, cudaStream_t s) 
     k_svd_left<<<(int)tasks.size(), 256, 0, s>>>(d, 0);
     CK_LAUNCH("k_svd_left(global)");
   }
+}
+
+// ---------------------------------------------------------------------------
+// Randomised left SVD (Sec. 2.4: the fill-in is compressed with the randomised
+// SVD of Halko et al.; reading R3b): for a block too tall for the exact
+// shared-memory SVD, a test matrix Omega (w x k, uniform in [-1, 1) from a
+// counter-based SplitMix64 stream), one power iteration with
+// re-orthonormalisation, B = Q^T M and the exact SVD of the k-row matrix B.
+// Returns the top k left singular vectors (a x k, ld a) and values.
+// ---------------------------------------------------------------------------
+__device__ __host__ inline unsigned long long splitmix64(unsigned long long x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+// O[e] = 2 u - 1, u = (splitmix64(seed + e) >> 11) 2^-53, e = i + c * rows
+__global__ void k_fill_uniform(double* __restrict__ O, long long n, unsigned long long seed) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long x = splitmix64(seed + (unsigned long long)e);
+    O[e] = 2.0 * ((double)(x >> 11) * 0x1.0p-53) - 1.0;
+  }
+}
+
+
+// inv[c] = 1 / s[c] where s[c] > 1e-10 s[0], else 0: drops numerically null
+// directions (above the SVD's basis-completion threshold 1e-13 a s[0], a <= 144)
+__global__ void k_inv_sigma(const InvSigma* __restrict__ t, int n) {
+  const int i = blockIdx.x;
+  if (i >= n) return;
+  const InvSigma T = t[i];
+  for (int c = threadIdx.x; c < T.k; c += blockDim.x)
+    T.inv[c] = (T.s[c] > 1e-10 * T.s[0] && T.s[c] > 0.0) ? 1.0 / T.s[c] : 0.0;
+}
+
+void run_inv_sigma(Arena& ar, const std::vector<InvSigma>& v, cudaStream_t s) {
+  if (v.empty()) return;
+  const InvSigma* d = upload(ar, v, s);
+  k_inv_sigma<<<(int)v.size(), 64, 0, s>>>(d, (int)v.size());
+  CK_LAUNCH("k_inv_sigma");
+}
+
+// Q = orth(X) for X (n x k, ld n): SVD of X^T, Q = X W diag(1/sigma)
+static void batched_orth(Arena& ar, const std::vector<const double*>& X, std::vector<double*>& Q,
+                         const std::vector<int>& n, int k, cudaStream_t s) {
+  const int nt = (int)X.size();
+  std::vector<CopyTask> tr;
+  std::vector<SvdTask> sv;
+  std::vector<InvSigma> iv;
+  std::vector<double*> XT(nt), W(nt), sg(nt), inv(nt), Ws(nt);
+  for (int t = 0; t < nt; t++) {
+    XT[t] = ar.alloc<double>((size_t)k * n[t]);
+    W[t] = ar.alloc<double>((size_t)k * k);
+    Ws[t] = ar.alloc<double>((size_t)k * k);
+    sg[t] = ar.alloc<double>(k);
+    inv[t] = ar.alloc<double>(k);
+    tr.push_back({X[t], XT[t], nullptr, n[t], k, k, n[t], 1, 0, 1.0, 0.0});
+    sv.push_back({XT[t], k, k, n[t], W[t], sg[t], nullptr});
+    iv.push_back({sg[t], inv[t], k});
+  }
+  std::vector<CopyTask> keep;
+  for (auto& c : tr) { validate(c); keep.push_back(c); }
+  launch_copy(upload(ar, keep, s), (int)keep.size(), s);
+  run_svd_left(ar, sv, s);
+  run_inv_sigma(ar, iv, s);
+  keep.clear();
+  for (int t = 0; t < nt; t++) {
+    CopyTask c{W[t], Ws[t], inv[t], k, k, k, k, 0, 0, 1.0, 0.0};
+    validate(c);
+    keep.push_back(c);
+  }
+  launch_copy(upload(ar, keep, s), (int)keep.size(), s);
+  std::vector<GemmTask> g;
+  for (int t = 0; t < nt; t++) g.push_back({X[t], Ws[t], Q[t], n[t], k, n[t], n[t], k, k, 0, 0, 1.0, 0.0});
+  run_gemms(ar, g, s);
+}
+
+unsigned long long rsvd_seed(int level, int box, int side) {
+  return splitmix64(((unsigned long long)level << 40) ^ ((unsigned long long)box << 2) ^
+                    (unsigned long long)side);
+}
+
+void run_rsvd_left(Arena& ar, const std::vector<RsvdTask>& tasks, cudaStream_t s) {
+  if (tasks.empty()) return;
+  const int nt = (int)tasks.size();
+  // tasks are grouped by k (all tasks of one call share k)
+  const int k = tasks[0].k;
+  for (auto& t : tasks)
+    if (t.k != k || t.k > SVD_SMEM_A || t.k > t.a)
+      throw Error(IFMM_ERR_CUDA, "internal: randomised SVD tasks need a common k <= 144 <= a");
+  std::vector<double*> Om(nt), Y(nt), Q(nt), Z(nt), Qz(nt), B(nt), WB(nt);
+  std::vector<GemmTask> g;
+  for (int t = 0; t < nt; t++) {
+    const RsvdTask& T = tasks[t];
+    Om[t] = ar.alloc<double>((size_t)T.w * k);
+    Y[t] = ar.alloc<double>((size_t)T.a * k);
+    Q[t] = ar.alloc<double>((size_t)T.a * k);
+    Z[t] = ar.alloc<double>((size_t)T.w * k);
+    Qz[t] = ar.alloc<double>((size_t)T.w * k);
+    B[t] = ar.alloc<double>((size_t)k * T.w);
+    WB[t] = ar.alloc<double>((size_t)k * k);
+    const long long n = (long long)T.w * k;
+    k_fill_uniform<<<(int)std::min<long long>(1024, (n + 255) / 256), 256, 0, s>>>(Om[t], n, T.seed);
+    CK_LAUNCH("k_fill_uniform");
+    g.push_back({T.M, Om[t], Y[t], T.ldm, T.w, T.a, T.a, k, T.w, 0, 0, 1.0, 0.0});  // Y = M Om
+  }
+  run_gemms(ar, g, s);
+  std::vector<int> na(nt), nw(nt);
+  std::vector<const double*> cY(Y.begin(), Y.end());
+  for (int t = 0; t < nt; t++) { na[t] = tasks[t].a; nw[t] = tasks[t].w; }
+  batched_orth(ar, cY, Q, na, k, s);
+  g.clear();
+  for (int t = 0; t < nt; t++)  // Z = M^T Q
+    g.push_back({tasks[t].M, Q[t], Z[t], tasks[t].ldm, tasks[t].a, tasks[t].w, tasks[t].w, k,
+                 tasks[t].a, 1, 0, 1.0, 0.0});
+  run_gemms(ar, g, s);
+  std::vector<const double*> cZ(Z.begin(), Z.end());
+  batched_orth(ar, cZ, Qz, nw, k, s);
+  g.clear();
+  for (int t = 0; t < nt; t++)  // Y = M Qz
+    g.push_back({tasks[t].M, Qz[t], Y[t], tasks[t].ldm, tasks[t].w, tasks[t].a, tasks[t].a, k,
+                 tasks[t].w, 0, 0, 1.0, 0.0});
+  run_gemms(ar, g, s);
+  batched_orth(ar, cY, Q, na, k, s);
+  g.clear();
+  for (int t = 0; t < nt; t++)  // B = Q^T M
+    g.push_back({Q[t], tasks[t].M, B[t], tasks[t].a, tasks[t].ldm, k, k, tasks[t].w, tasks[t].a,
+                 1, 0, 1.0, 0.0});
+  run_gemms(ar, g, s);
+  std::vector<SvdTask> sv;
+  for (int t = 0; t < nt; t++) sv.push_back({B[t], k, k, tasks[t].w, WB[t], tasks[t].sigma, nullptr});
+  run_svd_left(ar, sv, s);
+  g.clear();
+  for (int t = 0; t < nt; t++)  // W = Q W_B
+    g.push_back({Q[t], WB[t], tasks[t].W, tasks[t].a, k, tasks[t].a, tasks[t].a, k, k, 0, 0, 1.0, 0.0});
+  run_gemms(ar, g, s);
 }
 
 // ---------------------------------------------------------------------------

@@ -161,6 +161,7 @@ ifmm_system* system_create(ifmm_ctx* ctx, const double* pts, bool host, long lon
   require(opt->eps >= 0.0 && std::isfinite(opt->eps), "eps must be >= 0");
   require(opt->schur >= IFMM_P_FP64 && opt->schur <= IFMM_P_BF16, "unknown Schur precision");
   require(opt->rank_cap >= 0, "rank_cap must be >= 0");
+  require(opt->rsvd_rows >= 0 && opt->rsvd_rows <= SVD_EXACT_MAX_A, "rsvd_rows must be in 0..144");
   require(k->kind >= IFMM_K_INV_R && k->kind <= IFMM_K_PAPER_D, "unknown kernel kind");
   require(!(k->kind == IFMM_K_INV_R && std::isnan(k->diag)), "1/r kernel needs a diagonal");
   require(k->kind == IFMM_K_INV_R || k->param > 0.0, "kernel parameter must be > 0");

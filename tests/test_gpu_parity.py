@@ -137,6 +137,27 @@ def test_factor_solve_parity(ctx, name):
         ifmm.ifmm_system_destroy(sys)
 
 
+@pytest.mark.parametrize("name,cap,rows", [("3lev", 12, 20), ("c1", 10, 16), ("2d", 8, 16)])
+def test_randomised_recompression_parity(ctx, name, cap, rows):
+    """Blocks taller than `rows` under rank cap `cap` take the randomised SVD
+    (Sec. 2.4) on both sides, with the same counter-based test matrix."""
+    w = CASES[name]()
+    h2 = oracle_h2(w)
+    ora = IFMM(h2, w.eps, rank_cap=cap, rsvd_rows=rows)
+    sys = make_sys(ctx, w, tau=ora.tau, rank_cap=cap, rsvd_rows=rows)
+    fac = ifmm.ifmm_factor(ctx, sys)
+    try:
+        for l in range(2, h2.tree.L + 1):
+            assert ifmm.ifmm_factor_get_ranks(fac, l) == ora.ranks(l), f"ranks differ at depth {l}"
+        b = w.rhs(1)[:, 0]
+        x = torch.empty(w.N, dtype=torch.float64, device="cuda:0")
+        ifmm.ifmm_solve(ctx, fac, cuda(b), x, w.N)
+        assert rel(x.cpu().numpy(), ora.solve(b)) < 1e-9
+    finally:
+        ifmm.ifmm_factor_destroy(fac)
+        ifmm.ifmm_system_destroy(sys)
+
+
 def test_gmres_c1_direct_matches_dense_lu(ctx):
     """C1: GMRES with the exact matvec and the IFMM preconditioner reaches
     1e-10 and agrees with the dense LU solve of A (Sec. 3.2)."""

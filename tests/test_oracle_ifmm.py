@@ -134,3 +134,46 @@ def test_appendix_c_depth_first_closed_form():
     last = _eliminate(E, blocks, [0, 2, 3])
     expect = A11 - U1 @ V0.T @ np.linalg.solve(A00, U0) @ V1.T
     assert np.allclose(last, expect, atol=1e-11)
+
+
+def test_splitmix64_reference_value():
+    """The counter-based generator of the randomised SVD is SplitMix64
+    (Steele, Lea, Flood 2014): its first output from state 0 is fixed."""
+    from oracle.ifmm import splitmix64
+    assert int(splitmix64(np.uint64(0))) == 0xE220A8397B1DCDAF
+
+
+def test_rsvd_is_exact_for_low_rank_and_close_for_decaying_spectra():
+    """Randomised SVD (Sec. 2.4): exact when rank <= k, accurate for the leading
+    singular values of a fast-decaying spectrum."""
+    from oracle.ifmm import orth, rsvd_left, rsvd_seed
+    rng = np.random.default_rng(0)
+    U, _ = np.linalg.qr(rng.standard_normal((200, 200)))
+    V, _ = np.linalg.qr(rng.standard_normal((900, 200)))
+    s = np.zeros(200)
+    s[:30] = np.logspace(0, -9, 30)
+    M = (U * s) @ V.T
+    W, sr = rsvd_left(M, 40, rsvd_seed(3, 7, 0))
+    assert np.allclose(sr[:30], s[:30], rtol=1e-6, atol=1e-14)
+    assert np.linalg.norm(M - W[:, :30] @ (W[:, :30].T @ M)) < 1e-12
+    s2 = 10.0 ** (-np.arange(200) / 8.0)
+    M2 = (U * s2) @ V.T
+    W2, sr2 = rsvd_left(M2, 48, rsvd_seed(3, 8, 1))
+    assert np.allclose(sr2[:24], s2[:24], rtol=1e-8)
+    Q = orth(rng.standard_normal((50, 10)))
+    assert np.allclose(Q.T @ Q, np.eye(10), atol=1e-13)
+
+
+def test_randomised_recompression_keeps_error_bound():
+    """Blocks taller than rsvd_rows under a rank cap use the randomised
+    recompression (Sec. 2.4); the solve error stays at the eps level."""
+    N = 1500
+    w, h = setup(N, 7, 3, 24, 3, Kernel(K_INV_R, 0.0, 4.0 * N))
+    b = np.random.default_rng(1).standard_normal(N)
+    x = dense_solution(h, b)
+    f = IFMM(h, 1e-6, rank_cap=12, rsvd_rows=20)
+    assert max(f.level_a[2]) > 20
+    err = np.linalg.norm(f.solve(b) - x) / np.linalg.norm(x)
+    f0 = IFMM(h, 1e-6, rank_cap=12, sigma0=f.sigma0)
+    err0 = np.linalg.norm(f0.solve(b) - x) / np.linalg.norm(x)
+    assert err < 10 * max(err0, 1e-6)
