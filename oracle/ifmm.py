@@ -149,12 +149,17 @@ def uniform_test_matrix(rows: int, cols: int, seed) -> np.ndarray:
     return (2.0 * u - 1.0).reshape(cols, rows).T
 
 
-def orth(X: np.ndarray) -> np.ndarray:
-    """Orthonormal basis of range(X) from the SVD of X^T; directions with
-    sigma <= 1e-10 sigma_max are numerically null and dropped (zero columns)."""
+def _orth_once(X: np.ndarray) -> np.ndarray:
     W, s = left_svd(X.T)
     inv = np.where((s > 1e-10 * s[0]) & (s > 0), 1.0 / np.where(s > 0, s, 1.0), 0.0) if s.size else s
     return X @ (W * inv[None, :])
+
+
+def orth(X: np.ndarray) -> np.ndarray:
+    """Orthonormal basis of range(X) from the SVD of X^T, applied twice (the
+    second pass restores orthogonality lost in small-sigma directions);
+    directions with sigma <= 1e-10 sigma_max are numerically null and dropped."""
+    return _orth_once(_orth_once(X))
 
 
 def rsvd_left(M: np.ndarray, k: int, seed) -> tuple[np.ndarray, np.ndarray]:

@@ -741,7 +741,7 @@ void run_inv_sigma(Arena& ar, const std::vector<InvSigma>& v, cudaStream_t s) {
 }
 
 // Q = orth(X) for X (n x k, ld n): SVD of X^T, Q = X W diag(1/sigma)
-static void batched_orth(Arena& ar, const std::vector<const double*>& X, std::vector<double*>& Q,
+static void batched_orth_once(Arena& ar, const std::vector<const double*>& X, std::vector<double*>& Q,
                          const std::vector<int>& n, int k, cudaStream_t s) {
   const int nt = (int)X.size();
   std::vector<CopyTask> tr;
@@ -778,6 +778,17 @@ static void batched_orth(Arena& ar, const std::vector<const double*>& X, std::ve
 unsigned long long rsvd_seed(int level, int box, int side) {
   return splitmix64(((unsigned long long)level << 40) ^ ((unsigned long long)box << 2) ^
                     (unsigned long long)side);
+}
+
+// Orthonormalise twice: the second pass removes the loss of orthogonality the
+// first one suffers in directions with small singular values.
+static void batched_orth(Arena& ar, const std::vector<const double*>& X, std::vector<double*>& Q,
+                         const std::vector<int>& n, int k, cudaStream_t s) {
+  std::vector<double*> Q1(X.size());
+  for (size_t t = 0; t < X.size(); t++) Q1[t] = ar.alloc<double>((size_t)n[t] * k);
+  batched_orth_once(ar, X, Q1, n, k, s);
+  std::vector<const double*> cQ1(Q1.begin(), Q1.end());
+  batched_orth_once(ar, cQ1, Q, n, k, s);
 }
 
 void run_rsvd_left(Arena& ar, const std::vector<RsvdTask>& tasks, cudaStream_t s) {

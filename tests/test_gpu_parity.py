@@ -137,11 +137,24 @@ def test_factor_solve_parity(ctx, name):
         ifmm.ifmm_system_destroy(sys)
 
 
+WELL = {
+    "3lev": lambda: small_cube(3000, 7, cheb_n=3, leaf_max=32, eps=1e-6,
+                               kernel=Kernel(K_INV_R, 0.0, 4.0 * 3000)),
+    "c1": lambda: small_cube(2048, 1000, cheb_n=3, leaf_max=64, eps=1e-6,
+                             kernel=Kernel(K_INV_R, 0.0, 4.0 * 2048)),
+    "2d": lambda: small_cube(2500, 9, cheb_n=4, leaf_max=20, eps=1e-8, dim=2,
+                             kernel=Kernel(K_GAUSSIAN, 0.05, 3.0)),
+}
+
+
 @pytest.mark.parametrize("name,cap,rows", [("3lev", 12, 20), ("c1", 10, 16), ("2d", 8, 16)])
 def test_randomised_recompression_parity(ctx, name, cap, rows):
     """Blocks taller than `rows` under rank cap `cap` take the randomised SVD
-    (Sec. 2.4) on both sides, with the same counter-based test matrix."""
-    w = CASES[name]()
+    (Sec. 2.4) on both sides, with the same counter-based test matrix.  The
+    systems are well conditioned (strong diagonal) so that the comparison
+    measures the two implementations, not the amplification of rounding by
+    a large condition number."""
+    w = WELL[name]()
     h2 = oracle_h2(w)
     ora = IFMM(h2, w.eps, rank_cap=cap, rsvd_rows=rows)
     sys = make_sys(ctx, w, tau=ora.tau, rank_cap=cap, rsvd_rows=rows)
@@ -152,7 +165,7 @@ def test_randomised_recompression_parity(ctx, name, cap, rows):
         b = w.rhs(1)[:, 0]
         x = torch.empty(w.N, dtype=torch.float64, device="cuda:0")
         ifmm.ifmm_solve(ctx, fac, cuda(b), x, w.N)
-        assert rel(x.cpu().numpy(), ora.solve(b)) < 1e-9
+        assert rel(x.cpu().numpy(), ora.solve(b)) < 1e-10
     finally:
         ifmm.ifmm_factor_destroy(fac)
         ifmm.ifmm_system_destroy(sys)
