@@ -180,6 +180,24 @@ ifmm_status ifmm_solve(ifmm_ctx* ctx, const ifmm_factorization* fac, const doubl
 ifmm_status fmm_matvec(ifmm_ctx* ctx, const ifmm_system* sys, int mode, const double* x,
                        double* y, int nrhs, long long ld, ifmm_stream stream);
 
+/* ---- allocation-free matvec --------------------------------------------------- */
+/* The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory while they run (a host application that owns
+ * a fixed device pool, a real-time loop, code recording a CUDA graph).
+ * Computes the same y = A_n x as fmm_matvec(IFMM_MV_FMM) (the direct product
+ * when the system has no tree) but calls no cudaMalloc, cudaFree or other
+ * allocating routine: its scratch -- the tree lists it needs and the
+ * multipole / local coefficients -- lives in one file-scope device array of
+ * 64 MiB that every GPU loading the library holds until the process exits.
+ * A system and nrhs whose scratch exceeds 64 MiB are rejected with
+ * IFMM_ERR_INVALID_ARG and a message naming the bytes needed.
+ * The first call on a device looks up the array's address (device current);
+ * make that first call before any stream capture.  Every call shares the
+ * array and leaves its contents behind: calls that overlap on the GPU race.
+ * x, y: device, N x nrhs, ld >= N, must not alias. */
+ifmm_status fmm_matvec_static(ifmm_ctx* ctx, const ifmm_system* sys, const double* x, double* y,
+                              int nrhs, long long ld, ifmm_stream stream);
+
 /* ---- GMRES (Sec. 3.2) -------------------------------------------------------- */
 /* Non-restarted GMRES, x_0 = 0, CGS2 Arnoldi, Givens rotations, the
  * factorisation as right preconditioner (fac may be NULL: unpreconditioned).

@@ -108,6 +108,7 @@ def lib() -> C.CDLL:
                                   C.c_int, C.POINTER(GmresReport), P]),
         "gmres_solve_host": (C.c_int, [P, P, P, C.c_int, P, P, C.c_int, C.c_longlong,
                                        C.c_double, C.c_int, C.POINTER(GmresReport), P]),
+        "fmm_matvec_static": (C.c_int, [P, P, P, P, C.c_int, C.c_longlong, P]),
         "ifmm_profile_start": (C.c_int, [P]),
         "ifmm_profile_stop": (C.c_int, [P, C.POINTER(KernelStat), C.c_int, C.POINTER(C.c_int)]),
     }
@@ -250,6 +251,14 @@ def fmm_matvec(ctx, sys, mode: int, x, y, N: int, stream=None):
     py, k2, _ = _vec(y, N)
     assert k == k2
     _check(lib().fmm_matvec(ctx, sys, mode, px, py, k, ld, _stream(stream)), ctx)
+
+
+def fmm_matvec_static(ctx, sys, x, y, N: int, stream=None):
+    """y = A_n x without any device allocation (library-owned static scratch)."""
+    px, k, ld = _vec(x, N)
+    py, k2, _ = _vec(y, N)
+    assert k == k2
+    _check(lib().fmm_matvec_static(ctx, sys, px, py, k, ld, _stream(stream)), ctx)
 
 
 def gmres_solve(ctx, sys, fac, mode: int, b, x, N: int, tol=1e-10, maxit=500, stream=None):

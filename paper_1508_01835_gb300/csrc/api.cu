@@ -184,6 +184,16 @@ ifmm_status fmm_matvec(ifmm_ctx* ctx, const ifmm_system* sys, int mode, const do
   });
 }
 
+ifmm_status fmm_matvec_static(ifmm_ctx* ctx, const ifmm_system* sys, const double* x, double* y,
+                              int nrhs, long long ld, ifmm_stream stream) {
+  if (!ctx || !sys || !x || !y || nrhs < 0) return IFMM_ERR_INVALID_ARG;
+  if (ld < sys->N || x == y) return IFMM_ERR_INVALID_ARG;
+  return guard(ctx, [&] {
+    CK(cudaSetDevice(ctx->device));
+    system_matvec_static(const_cast<ifmm_system*>(sys), x, y, nrhs, ld, ctx->device, st(stream));
+  });
+}
+
 ifmm_status gmres_solve(ifmm_ctx* ctx, const ifmm_system* sys, const ifmm_factorization* fac,
                         int mode, const double* b, double* x, int nrhs, long long ld, double tol,
                         int maxit, ifmm_gmres_report* rep, ifmm_stream stream) {

@@ -147,4 +147,6 @@ ifmm_system* system_create(ifmm_ctx* ctx, const double* pts, bool host, long lon
 void system_matvec(ifmm_system* sys, int mode, const double* x, long long ldx, double* y,
                    long long ldy, int nrhs, cudaStream_t s);
 double system_sigma0(ifmm_system* sys, cudaStream_t s, int* iters);
+void system_matvec_static(ifmm_system* sys, const double* x, double* y, int nrhs, long long ld,
+                          int device, cudaStream_t s);
 }  // namespace ifmm
