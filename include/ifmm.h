@@ -76,7 +76,7 @@ typedef struct {
   int fmm_n;           /* Chebyshev order of fmm_matvec; 0 = cheb_n                 */
   int rsvd_rows;       /* blocks with more rows than this (and a rank cap below
                           their height) are recompressed with the randomised SVD
-                          of Sec. 2.4; 0 = 144, otherwise 1..144                   */
+                          of Sec. 2.4; 0 = 64, otherwise 1..144                    */
 } ifmm_options;
 
 typedef enum { IFMM_MV_FMM = 0, IFMM_MV_DIRECT = 1 } ifmm_matvec_mode;

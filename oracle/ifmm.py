@@ -51,8 +51,8 @@ R7  parent bases are initialised after the children's level is eliminated
 R8  pivoting: partial (row) pivoting inside E(P, P) only (LAPACK getrf).
 R9  an optional rank cap bounds r (default here: none; the CUDA library's
     default is n^D, the rank of the initial Chebyshev representation).
-R3b blocks taller than 144 rows that are truncated below their height are
-    recompressed with the randomised SVD of the paper's Sec. 2.4 (Halko et
+R3b blocks taller than rsvd_rows rows (default 64) that are truncated below
+    their height are recompressed with the randomised SVD of Sec. 2.4 (Halko et
     al.): k = min(a, cap + 16, 144) columns of a uniform [-1, 1) test matrix
     drawn from a counter-based SplitMix64 stream (seeded by level, box and
     side, so the CUDA path draws the same numbers), one power iteration with
@@ -121,6 +121,7 @@ def left_svd(M: np.ndarray):
 
 
 SVD_EXACT_MAX_A = 144
+RSVD_ROWS_DEFAULT = 64
 RSVD_OVERSAMPLE = 16
 _M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
 
@@ -218,7 +219,7 @@ class IFMM:
     """Plain IFMM factorisation of the H^2 matrix A_n defined by ``h2``."""
 
     def __init__(self, h2: H2, eps: float, tau: float | None = None, rank_cap: int | None = None,
-                 sigma0: float | None = None, rsvd_rows: int = SVD_EXACT_MAX_A):
+                 sigma0: float | None = None, rsvd_rows: int = RSVD_ROWS_DEFAULT):
         self.h2 = h2
         self.rsvd_rows = rsvd_rows
         self.tree = h2.tree

@@ -28,11 +28,12 @@ using Clock = std::chrono::steady_clock;
 static double since(Clock::time_point t) {
   return std::chrono::duration<double>(Clock::now() - t).count();
 }
-// IFMM_TRACE=1: one line per phase on stderr (sizes, ranks, seconds)
+// IFMM_TRACE=1: one line per phase on stderr (sizes, ranks, seconds);
+// IFMM_TRACE=2 adds one line per SVD launch
 static bool tracing() {
   static const bool v = [] {
     const char* e = std::getenv("IFMM_TRACE");
-    return e && e[0] == '1';
+    return e && (e[0] == '1' || e[0] == '2');
   }();
   return v;
 }
@@ -83,11 +84,12 @@ struct FLevel {
   Arena mem;
 };
 
-// Tall blocks are recompressed with the randomised SVD when the rank cap is
-// below the block height and truncation is on (tau > 0): the top
-// k = min(a, cap + oversampling, 144) singular triplets decide the rank.
+// Blocks taller than rsvd_rows (default 64) are recompressed with the
+// randomised SVD when the rank cap is below the block height and truncation
+// is on (tau > 0): the top k = min(a, cap + oversampling, 144) singular
+// triplets decide the rank.
 static double g_tau_for_rsvd = 0.0;
-static int g_rsvd_rows = SVD_EXACT_MAX_A;
+static int g_rsvd_rows = RSVD_ROWS_DEFAULT;
 static bool use_rsvd(int a, int rcap) {
   return g_tau_for_rsvd > 0.0 && a > g_rsvd_rows && rcap < a;
 }
@@ -605,12 +607,17 @@ struct Factorizer {
       g.push_back(gm(WV[t], a, 1, st.V[j], a, 0, tm[t], std::max(rn[t], 1), rn[t], st.r[j], a, 1.0, 0.0));
     }
     run_gemms(scratch, g, s);
-    // Algorithm 3: K(j, q) <- r_j K(j, q), K(q, j) <- K(q, j) t_j^T (q in I_j)
-    std::set<std::pair<int, int>> edges;
+    // Algorithm 3: K(j, q) <- r_j K(j, q), K(q, j) <- K(q, j) t_j^T (q in I_j).
+    // Each edge once: (j, q) from j's list; (q, j) from j's list only when q is
+    // not recompressed itself (otherwise q's list adds it).
+    std::vector<std::pair<int, int>> edges;
+    std::vector<char> isR(st.nb, 0);
+    for (int j : J) isR[j] = 1;
     for (int j : J)
       for (int k = lv.far_ptr[j]; k < lv.far_ptr[j + 1]; k++) {
-        edges.insert({j, lv.far[k]});
-        edges.insert({lv.far[k], j});
+        const int q = lv.far[k];
+        edges.push_back({j, q});
+        if (!isR[q]) edges.push_back({q, j});
       }
     auto rold = [&](int b) { return st.r[b]; };
     auto rnew = [&](int b) { auto it = slot.find(b); return it == slot.end() ? st.r[b] : rn[it->second]; };
@@ -790,7 +797,7 @@ struct Factorizer {
     f->info.sigma0_iters = sys->sigma0_iters;
     f->info.tau = tau;
     g_tau_for_rsvd = tau;
-    g_rsvd_rows = o.rsvd_rows > 0 ? o.rsvd_rows : SVD_EXACT_MAX_A;
+    g_rsvd_rows = o.rsvd_rows > 0 ? o.rsvd_rows : RSVD_ROWS_DEFAULT;
     cap_global = o.rank_cap > 0 ? o.rank_cap : (tau == 0.0 ? (1 << 30) : nd);
     f->rank.assign(L + 1, {});
     f->yoff.assign(L + 1, {});

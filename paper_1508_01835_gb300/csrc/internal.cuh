@@ -279,7 +279,8 @@ struct RsvdTask {
   double* sigma;
 };
 void run_rsvd_left(Arena& ar, const std::vector<RsvdTask>& tasks, cudaStream_t s);
-constexpr int SVD_EXACT_MAX_A = 144;  // larger blocks use run_rsvd_left when truncating
+constexpr int SVD_EXACT_MAX_A = 144;  // largest block the exact shared-memory SVD takes
+constexpr int RSVD_ROWS_DEFAULT = 64;  // truncated blocks taller than this use run_rsvd_left
 constexpr int RSVD_OVERSAMPLE = 16;
 unsigned long long rsvd_seed(int level, int box, int side);
 // inv[c] = 1 / s[c] where s[c] > 1e-10 s[0], else 0

@@ -10,6 +10,10 @@
 
 #include "internal.cuh"
 
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
+
 namespace ifmm {
 
 // ---------------------------------------------------------------------------
@@ -125,6 +129,73 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmTask* __restrict__ tasks
   }
 }
 
+// Small tiles for small products (M, N <= 32): 32 x 32 outputs, 64 threads
+// with 4 x 4 each, so a 16 x 16 result does not pay for a 64 x 64 tile.
+constexpr int ST = 32;
+__global__ void __launch_bounds__(64) k_gemm_small(const GemmTask* __restrict__ tasks,
+                                                   const GemmTile* __restrict__ tiles) {
+  const GemmTile tl = tiles[blockIdx.x];
+  const GemmTask t = tasks[tl.task];
+  __shared__ double As[GK][ST + 1];
+  __shared__ double Bs[GK][ST + 1];
+  const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; i++)
+#pragma unroll
+    for (int j = 0; j < 4; j++) acc[i][j] = 0.0;
+  for (int k0 = 0; k0 < t.K; k0 += GK) {
+    for (int idx = threadIdx.x; idx < ST * GK; idx += 64) {
+      int m, k;
+      if (t.transA) { k = idx % GK; m = idx / GK; }
+      else { m = idx % ST; k = idx / ST; }
+      const int gm = tl.m0 + m, gk = k0 + k;
+      double v = 0.0;
+      if (gm < t.M && gk < t.K)
+        v = t.transA ? t.A[gk + (long long)gm * t.lda] : t.A[gm + (long long)gk * t.lda];
+      As[k][m] = v;
+    }
+    for (int idx = threadIdx.x; idx < ST * GK; idx += 64) {
+      int n, k;
+      if (t.transB) { n = idx % ST; k = idx / ST; }
+      else { k = idx % GK; n = idx / GK; }
+      const int gn = tl.n0 + n, gk = k0 + k;
+      double v = 0.0;
+      if (gn < t.N && gk < t.K)
+        v = t.transB ? t.B[gn + (long long)gk * t.ldb] : t.B[gk + (long long)gn * t.ldb];
+      Bs[k][n] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < GK; k++) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; i++) a[i] = As[k][ty + 8 * i];
+#pragma unroll
+      for (int j = 0; j < 4; j++) b[j] = Bs[k][tx + 8 * j];
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    const int gm = tl.m0 + ty + 8 * i;
+    if (gm >= t.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      const int gn = tl.n0 + tx + 8 * j;
+      if (gn >= t.N) continue;
+      double* c = t.C + gm + (long long)gn * t.ldc;
+      *c = (t.beta == 0.0) ? t.alpha * acc[i][j] : t.beta * (*c) + t.alpha * acc[i][j];
+    }
+  }
+}
+
+static inline bool small_task(const GemmTask& t) { return t.M <= ST && t.N <= ST; }
+
 void gemm_tiles(const GemmTask& t, int ti, std::vector<GemmTile>& tiles) {
   if (t.M <= 0 || t.N <= 0) return;
   for (int n0 = 0; n0 < t.N; n0 += GT)
@@ -139,14 +210,28 @@ void launch_gemm(const GemmTask* d_tasks, const GemmTile* d_tiles, int ntiles, c
   CK_LAUNCH("k_gemm");
 }
 
+static void launch_gemm_small(const GemmTask* d_tasks, const GemmTile* d_tiles, int ntiles,
+                              cudaStream_t s, double flops) {
+  if (ntiles <= 0) return;
+  Prof p("k_gemm_fp64_small", flops, 0.0, s);
+  k_gemm_small<<<ntiles, 64, 0, s>>>(d_tasks, d_tiles);
+  CK_LAUNCH("k_gemm_small");
+}
+
 void run_gemms(Arena& ar, const std::vector<GemmTask>& tasks, cudaStream_t s) {
   if (tasks.empty()) return;
-  std::vector<GemmTask> kept;
-  std::vector<GemmTile> tiles;
-  double flops = 0.0;
+  std::vector<GemmTask> kept, kept_s;
+  std::vector<GemmTile> tiles, tiles_s;
+  double flops = 0.0, flops_s = 0.0;
   for (const GemmTask& t : tasks) {
     if (t.M <= 0 || t.N <= 0) continue;
     validate(t);
+    if (t.K > 0 && small_task(t)) {
+      flops_s += 2.0 * t.M * (double)t.N * t.K;
+      tiles_s.push_back({(int)kept_s.size(), 0, 0});
+      kept_s.push_back(t);
+      continue;
+    }
     if (t.K > 0) flops += 2.0 * t.M * (double)t.N * t.K;
     if (t.K <= 0) {
       // C = beta C: express as a copy task with zero source
@@ -158,6 +243,9 @@ void run_gemms(Arena& ar, const std::vector<GemmTask>& tasks, cudaStream_t s) {
     gemm_tiles(t, (int)kept.size(), tiles);
     kept.push_back(t);
   }
+  if (!tiles_s.empty())
+    launch_gemm_small(upload(ar, kept_s, s), upload(ar, tiles_s, s), (int)tiles_s.size(), s,
+                      flops_s);
   if (tiles.empty()) return;
   const GemmTask* dt = upload(ar, kept, s);
   const GemmTile* dl = upload(ar, tiles, s);
@@ -574,33 +662,41 @@ __device__ void jacobi_columns(double* L, int lda, int a, double* red) {
   }
 }
 
-__global__ void __launch_bounds__(256) k_svd_left(const SvdTask* __restrict__ tasks, int use_smem) {
+// cw: columns streamed per chunk (shared-memory mode); the reflector vector
+// lives behind the chunk in dynamic shared memory.
+__global__ void __launch_bounds__(1024) k_svd_left(const SvdTask* __restrict__ tasks, int use_smem,
+                                                   int cw_max) {
   const SvdTask t = tasks[blockIdx.x];
   const int a = t.a;
   if (a <= 0) return;
   if ((a <= SVD_SMEM_A) != (use_smem != 0)) return;
   extern __shared__ double sm[];
   __shared__ double red[40];
-  __shared__ double vsh[SVD_CW];
+  __shared__ double vsh_g[SVD_CW];
   SvdView v;
+  double* vsh;
+  int cwm;
   if (use_smem) {
     v.L = sm;
     v.lda = a + 1;                 // odd stride: no bank conflicts on row access
     v.C = sm + (size_t)(a + 1) * a;
     v.ldc = a + 1;
+    vsh = v.C + (size_t)(a + 1) * cw_max;
+    cwm = cw_max;
   } else {
     v.L = t.work;
     v.lda = a;
     v.C = t.work + (size_t)a * a;
     v.ldc = a;
+    vsh = vsh_g;
+    cwm = SVD_CW;
   }
-  // L starts as the first min(a, w) columns of M, lower-triangularised by the
-  // first chunk pass: initialise L = 0 and stream all columns as chunks.
+  // L starts at zero; every column of M is streamed through the chunk C and
+  // annihilated against L (the reflector treats L[k,k] as its first entry).
   for (int e = threadIdx.x; e < a * a; e += blockDim.x) v.L[(e % a) + (e / a) * v.lda] = 0.0;
   __syncthreads();
-  // the diagonal of L starts at 0: the reflector treats L[k,k] as x0
-  for (int c0 = 0; c0 < t.w; c0 += SVD_CW) {
-    const int cw = min(SVD_CW, t.w - c0);
+  for (int c0 = 0; c0 < t.w; c0 += cwm) {
+    const int cw = min(cwm, t.w - c0);
     for (int e = threadIdx.x; e < a * cw; e += blockDim.x) {
       const int r = e % a, c = e / a;
       v.C[r + c * v.ldc] = t.M[r + (long long)(c0 + c) * t.ldm];
@@ -609,9 +705,9 @@ __global__ void __launch_bounds__(256) k_svd_left(const SvdTask* __restrict__ ta
     lq_chunk(v, a, cw, red, vsh);
   }
   jacobi_columns(v.L, v.lda, a, red);
-  // sigma_j = |L_j|; order by decreasing sigma (ties: lower column first)
-  double* sig = vsh;  // reuse when a <= SVD_CW, otherwise the scratch column of C
-  double* sg = (a <= SVD_CW) ? sig : v.C;
+  // sigma_j = |L_j|; order by decreasing sigma (ties: lower column first).
+  // The chunk area (>= a doubles) is free now and holds the column norms.
+  double* sg = v.C;
   for (int j = threadIdx.x; j < a; j += blockDim.x) {
     double s = 0.0;
     for (int r = 0; r < a; r++) { const double x = v.L[r + j * v.lda]; s += x * x; }
@@ -661,8 +757,23 @@ __global__ void __launch_bounds__(256) k_svd_left(const SvdTask* __restrict__ ta
   }
 }
 
+// IFMM_TRACE=2: one line per SVD launch on stderr (tasks, shapes, seconds);
+// synchronises the stream around each launch.
+static bool svd_tracing() {
+  static const bool v = [] {
+    const char* e = std::getenv("IFMM_TRACE");
+    return e && e[0] == '2';
+  }();
+  return v;
+}
+
 void run_svd_left(Arena& ar, const std::vector<SvdTask>& tasks, cudaStream_t s) {
   if (tasks.empty()) return;
+  std::chrono::steady_clock::time_point t0;
+  if (svd_tracing()) {
+    CK(cudaStreamSynchronize(s));
+    t0 = std::chrono::steady_clock::now();
+  }
   for (auto& t : tasks) {
     if (t.a <= 0) continue;
     Ranges::check(t.M, mat_bytes(t.a, t.w, t.ldm), "svd M");
@@ -682,19 +793,37 @@ void run_svd_left(Arena& ar, const std::vector<SvdTask>& tasks, cudaStream_t s) 
   for (auto& t : tasks) fl += 2.0 * t.a * (double)t.a * t.w;
   Prof p("k_svd_left", fl, 0.0, s);
   if (amax_s > 0) {
-    const size_t smem = sizeof(double) * (size_t)(amax_s + 1) * (amax_s + SVD_CW);
+    // widest chunk that fits next to L: (a+1)(a+cw) + cw doubles <= 200 KiB
+    const long long budget = (200 * 1024) / 8;
+    long long cw = (budget - (long long)(amax_s + 1) * amax_s) / (amax_s + 2);
+    int wmax = 0;
+    for (auto& t : tasks) if (t.a <= SVD_SMEM_A) wmax = std::max(wmax, t.w);
+    cw = std::min<long long>(cw, 2048);
+    cw = std::min<long long>(cw, std::max(wmax, 1));
+    cw = std::max<long long>(cw, SVD_CW);
+    const size_t smem = sizeof(double) * ((size_t)(amax_s + 1) * (amax_s + cw) + cw);
     static bool attr = false;
     if (!attr) {
       CK(cudaFuncSetAttribute(k_svd_left, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               200 * 1024));
       attr = true;
     }
-    k_svd_left<<<(int)tasks.size(), 256, smem, s>>>(d, 1);
+    const int threads = amax_s > 96 ? 512 : 256;
+    k_svd_left<<<(int)tasks.size(), threads, smem, s>>>(d, 1, (int)cw);
     CK_LAUNCH("k_svd_left(smem)");
   }
   if (big) {
-    k_svd_left<<<(int)tasks.size(), 256, 0, s>>>(d, 0);
+    k_svd_left<<<(int)tasks.size(), 512, 0, s>>>(d, 0, SVD_CW);
     CK_LAUNCH("k_svd_left(global)");
+  }
+  if (svd_tracing()) {
+    CK(cudaStreamSynchronize(s));
+    int amax = 0, wmax = 0;
+    double wsum = 0.0;
+    for (auto& t : tasks) { amax = std::max(amax, t.a); wmax = std::max(wmax, t.w); wsum += t.w; }
+    std::fprintf(stderr, "[svd] tasks %zu, max a %d, max w %d, avg w %.0f, %.4f s\n", tasks.size(),
+                 amax, wmax, wsum / tasks.size(),
+                 std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
   }
 }
 
