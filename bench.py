@@ -291,7 +291,7 @@ def run_ours(args):
                "d2h_bytes_per_step": int(b_h.nbytes)}
 
     # roofline of the dominant kernel, from the library's own event timings
-    kern_stats = {k: v for k, v in stats.items() if not k.startswith("(")}
+    kern_stats = {k: v for k, v in stats.items() if not k.startswith("(") and ":" not in k}
     dom = max(kern_stats.items(), key=lambda kv: kv[1][1]) if kern_stats else None
     roofline = None
     if dom:

@@ -71,12 +71,12 @@ typedef struct {
                           0 disables compression (exact block LU of E)             */
   int schur;           /* ifmm_precision of the Schur products                      */
   double tau_override; /* > 0: use this absolute threshold instead of eps*sigma_0   */
-  int rank_cap;        /* >= 1: cap on every box rank; 0 = automatic (2 n^D, or no
+  int rank_cap;        /* >= 1: cap on every box rank; 0 = automatic (n^D, or no
                           cap when eps == 0)                                        */
   int fmm_n;           /* Chebyshev order of fmm_matvec; 0 = cheb_n                 */
   int rsvd_rows;       /* blocks with more rows than this (and a rank cap below
                           their height) are recompressed with the randomised SVD
-                          of Sec. 2.4; 0 = 64, otherwise 1..144                    */
+                          of Sec. 2.4; 0 = 160, otherwise 1..65536                 */
 } ifmm_options;
 
 typedef enum { IFMM_MV_FMM = 0, IFMM_MV_DIRECT = 1 } ifmm_matvec_mode;

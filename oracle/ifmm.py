@@ -51,7 +51,7 @@ R7  parent bases are initialised after the children's level is eliminated
 R8  pivoting: partial (row) pivoting inside E(P, P) only (LAPACK getrf).
 R9  an optional rank cap bounds r (default here: none; the CUDA library's
     default is n^D, the rank of the initial Chebyshev representation).
-R3b blocks taller than rsvd_rows rows (default 64) that are truncated below
+R3b blocks taller than rsvd_rows rows (default 160) that are truncated below
     their height are recompressed with the randomised SVD of Sec. 2.4 (Halko et
     al.): k = min(a, cap + 16, 144) columns of a uniform [-1, 1) test matrix
     drawn from a counter-based SplitMix64 stream (seeded by level, box and
@@ -121,7 +121,7 @@ def left_svd(M: np.ndarray):
 
 
 SVD_EXACT_MAX_A = 144
-RSVD_ROWS_DEFAULT = 64
+RSVD_ROWS_DEFAULT = 160
 RSVD_OVERSAMPLE = 16
 _M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
 

@@ -84,7 +84,7 @@ struct FLevel {
   Arena mem;
 };
 
-// Blocks taller than rsvd_rows (default 64) are recompressed with the
+// Blocks taller than rsvd_rows (default 160) are recompressed with the
 // randomised SVD when the rank cap is below the block height and truncation
 // is on (tau > 0): the top k = min(a, cap + oversampling, 144) singular
 // triplets decide the rank.
@@ -580,10 +580,8 @@ struct Factorizer {
         rsvd.push_back({MV[t], a, a, wV[t], kk[t], rsvd_seed(lv.l, j, 1), WV[t], sV[t]});
         f->info.flops_lowrank += 8.0 * a * (double)kk[t] * (wU[t] + wV[t]);
       } else {
-        double* wk1 = a > 144 ? scratch.alloc<double>((size_t)a * a + (size_t)a * 32) : nullptr;
-        double* wk2 = a > 144 ? scratch.alloc<double>((size_t)a * a + (size_t)a * 32) : nullptr;
-        svd.push_back({MU[t], a, a, wU[t], WU[t], sU[t], wk1});
-        svd.push_back({MV[t], a, a, wV[t], WV[t], sV[t], wk2});
+        svd.push_back({MU[t], a, a, wU[t], WU[t], sU[t], nullptr});
+        svd.push_back({MV[t], a, a, wV[t], WV[t], sV[t], nullptr});
         f->info.flops_lowrank += 4.0 * a * (double)a * (wU[t] + wV[t]);
       }
       rt.push_back({sU[t], sV[t], kk[t], st.rcap[j], d_r + t, d_counters});

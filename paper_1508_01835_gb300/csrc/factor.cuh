@@ -32,12 +32,11 @@ struct SolvePlan {
     CopyTask* copies = nullptr;
     int ncopies = 0;
     GetrsPlan rs;
-    SpRow* rows = nullptr;
-    SpEnt* ents = nullptr;
-    int nrows = 0;
+    SpmmPlan sp;
   };
   std::vector<Step> steps;
   Arena task_mem;
+  GraphCache graph;  // the steps (and the ybar clears) as one graph
 };
 
 }  // namespace ifmm

@@ -6,6 +6,7 @@
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <stdexcept>
@@ -107,14 +108,46 @@ void* begin(const char* name, double flops, double bytes, cudaStream_t s);
 void end(void* token, cudaStream_t s);
 void start();
 int stop(ifmm_kernel_stat* out, int capacity);
+// While a launch sequence is captured into a graph, profiled launches add
+// their flops and bytes here instead of recording events.
+struct Capture { double flops = 0.0, bytes = 0.0; };
+Capture*& capture();
 }  // namespace prof
 struct Prof {
-  void* tok;
+  void* tok = nullptr;
   cudaStream_t s;
-  Prof(const char* name, double flops, double bytes, cudaStream_t st)
-      : tok(prof::enabled() ? prof::begin(name, flops, bytes, st) : nullptr), s(st) {}
+  Prof(const char* name, double flops, double bytes, cudaStream_t st) : s(st) {
+    if (prof::Capture* c = prof::capture()) {
+      c->flops += flops;
+      c->bytes += bytes;
+      return;
+    }
+    if (prof::enabled()) tok = prof::begin(name, flops, bytes, st);
+  }
   ~Prof() { if (tok) prof::end(tok, s); }
 };
+
+// A fixed launch sequence replayed as one CUDA graph.  The sequence is
+// captured on a private stream the first time (and again when `key` changes)
+// and launched on the caller's stream; a profiled replay is one entry named
+// `name` carrying the summed flops and bytes of the captured launches, and
+// each replay adds the captured kernel count to the launch counter.
+// IFMM_GRAPHS=0 runs the sequence directly instead.
+struct GraphCache {
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cs = nullptr;
+  long long key = -1;
+  unsigned long long kernels = 0;
+  double flops = 0.0, bytes = 0.0;
+  GraphCache() = default;
+  GraphCache(const GraphCache&) = delete;
+  GraphCache& operator=(const GraphCache&) = delete;
+  void reset();
+  ~GraphCache();
+};
+bool graphs_enabled();
+void run_graph(GraphCache& g, long long key, const char* name, cudaStream_t s,
+               const std::function<void(cudaStream_t)>& body);
 
 // ---------------------------------------------------------------------------
 // Device memory: a chunked bump allocator.  Blocks are 256-byte aligned.
@@ -252,14 +285,34 @@ struct GetrsPlan {
   const RsTask* d = nullptr;
   int nt = 0, nmax = 0, gy = 1;
   std::vector<GemmLaunch> fwd, bwd;  // per panel, forward / backward order
+  // Few right-hand sides (<= GETRS_SMALL_COLS): solved panel by panel, every
+  // panel one launch over all tasks, with the inverses of the diagonal blocks
+  // formed once when the plan is made.
+  bool panel = false;
+  const struct RsPanel* pd = nullptr;
+  int nblk_max = 0;
+};
+constexpr int GETRS_SMALL_COLS = 8;
+constexpr int GETRS_PANEL = 64;   // panel width of the panel solve
+constexpr int GETRS_PROWS = 128;  // rows of the update per CTA
+struct RsPanel {
+  const double* LU;
+  int lda, n;
+  const int* perm;  // row interchanges as a gather index: (P b)[i] = b[perm[i]]
+  double* B;
+  int ldb, ncols;
+  double *w1, *w2;  // n x ncols each (ld n): gathered input / forward result
+  double* dinv;     // 2 nblk blocks of 64 x 64 (ld 64): inverses of the diagonal
+                    // blocks of L (unit lower), then of U
+  int nblk;
 };
 GetrsPlan plan_getrs(Arena& ar, const std::vector<RsTask>& tasks, cudaStream_t s);
 void exec_getrs(const GetrsPlan& p, cudaStream_t s);
 
 // Left singular vectors and values of M (a x w, a <= w after zero padding is
 // implied): W (a x a, ld a) and sigma (a), sorted by decreasing sigma.
-// work: a*w + a*a doubles of scratch (only used when the matrix is too big for
-// shared memory).
+// work: a*a + 16a doubles of scratch for a > SVD_SMEM_A (null: taken from the
+// arena given to run_svd_left); unused otherwise.
 struct SvdTask {
   const double* M;
   int ldm, a, w;
@@ -279,8 +332,10 @@ struct RsvdTask {
   double* sigma;
 };
 void run_rsvd_left(Arena& ar, const std::vector<RsvdTask>& tasks, cudaStream_t s);
-constexpr int SVD_EXACT_MAX_A = 144;  // largest block the exact shared-memory SVD takes
-constexpr int RSVD_ROWS_DEFAULT = 64;  // truncated blocks taller than this use run_rsvd_left
+constexpr int SVD_EXACT_MAX_A = 144;  // largest k of the randomised SVD
+constexpr int SVD_SMEM_A = 160;       // largest block the shared-memory SVD takes
+constexpr int SVD_SMEM_BUDGET = 29000;  // doubles of dynamic shared memory per SVD CTA
+constexpr int RSVD_ROWS_DEFAULT = 160;  // truncated blocks taller than this use run_rsvd_left
 constexpr int RSVD_OVERSAMPLE = 16;
 unsigned long long rsvd_seed(int level, int box, int side);
 // inv[c] = 1 / s[c] where s[c] > 1e-10 s[0], else 0
@@ -321,8 +376,37 @@ struct SpEnt {
   int lda, k, transA;
   double alpha;
 };
-void launch_spmm(const SpRow* rows, int nrows, const SpEnt* ents, int nrhs, cudaStream_t s,
-                 double flops = 0.0, double bytes = 0.0);
 void validate_spmm(const std::vector<SpRow>& rows, const std::vector<SpEnt>& ents, int nrhs);
+
+// Work split of one launch.  A job sums one contiguous range of a row's
+// concatenated columns (entries in order, each contributing k columns) over
+// segments; a row whose work exceeds the per-job target is split over several
+// jobs that write partial sums, and a second pass adds them in job order, so
+// results do not depend on scheduling.
+struct SpJob {
+  int row, s0, ns;
+  long long part;  // offset of this job's partial sums; < 0: the job writes y
+};
+struct SpSeg { int ent, k0, k1; };
+struct SpRed {
+  int row, nj;
+  long long base;  // partial sums of job j of the row at base + j * m
+};
+struct SpmmPlan {
+  const SpRow* rows = nullptr;
+  const SpEnt* ents = nullptr;
+  const SpJob* jobs = nullptr;
+  const SpSeg* segs = nullptr;
+  const SpRed* reds = nullptr;
+  int njobs = 0, nreds = 0;
+  double* part = nullptr;   // partial sums: part[job.part + r + c * part_ld]
+  long long part_ld = 0;
+  int cap = 0;              // right-hand sides per pass
+  double flops = 0.0, bytes = 0.0;  // per right-hand side
+};
+// Plans rows/ents (uploaded to `ar`, with room for `cap` right-hand sides).
+SpmmPlan plan_spmm(Arena& ar, const std::vector<SpRow>& rows, const std::vector<SpEnt>& ents,
+                   int cap, cudaStream_t s);
+void launch_spmm(const SpmmPlan& p, int nrhs, cudaStream_t s);
 
 }  // namespace ifmm

@@ -58,6 +58,7 @@ void validate(const GemmTask& t) {
 void launch_copy(const CopyTask* d_tasks, int ntasks, cudaStream_t s) {
   if (ntasks <= 0) return;
   dim3 grid(ntasks, 16);
+  Prof p("k_copy", 0.0, 0.0, s);
   k_copy<<<grid, 256, 0, s>>>(d_tasks);
   CK_LAUNCH("k_copy");
 }
@@ -483,6 +484,133 @@ __global__ void k_trsm_rhs(const RsTask* __restrict__ tasks, int k0, int upper) 
   }
 }
 
+// Row interchanges of LAPACK getrf (swap j <-> piv[j], j = 0..n-1 in order)
+// as a gather index: (P b)[i] = b[perm[i]].  One thread per task.
+__global__ void k_piv_to_perm(const RsTask* __restrict__ tasks, int* const* perm, int nt) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  const RsTask T = tasks[t];
+  int* p = perm[t];
+  for (int i = 0; i < T.n; i++) p[i] = i;
+  for (int j = 0; j < T.n; j++) {
+    const int q = T.piv[j];
+    if (q != j) { const int tmp = p[j]; p[j] = p[q]; p[q] = tmp; }
+  }
+}
+
+// Inverse of one jb x jb diagonal block (jb <= 64) of L (unit lower, z = 0)
+// or U (upper, z = 1): thread j forms column j of the inverse by
+// substitution against e_j; the block is stored zero-padded, ld 64.
+__global__ void __launch_bounds__(64) k_getrs_dinv(const RsPanel* __restrict__ tasks) {
+  const RsPanel t = tasks[blockIdx.y];
+  const int b = blockIdx.x, upper = blockIdx.z;
+  if (b >= t.nblk) return;
+  const int k0 = b * GETRS_PANEL, jb = min(GETRS_PANEL, t.n - k0);
+  const long long lda = t.lda;
+  const double* T = t.LU + k0 + k0 * lda;
+  __shared__ double X[GETRS_PANEL][GETRS_PANEL + 1];  // X[i][j]: row i of column j
+  const int j = threadIdx.x;
+  for (int i = 0; i < GETRS_PANEL; i++) X[i][j] = 0.0;
+  if (j < jb) {
+    if (!upper) {
+      X[j][j] = 1.0;
+      for (int i = j + 1; i < jb; i++) {
+        double s = 0.0;
+        for (int q = j; q < i; q++) s = fma(T[i + q * lda], X[q][j], s);
+        X[i][j] = -s;
+      }
+    } else {
+      for (int i = j; i >= 0; i--) {
+        double s = (i == j) ? 1.0 : 0.0;
+        for (int q = i + 1; q <= j; q++) s = fma(-T[i + q * lda], X[q][j], s);
+        double d = T[i + i * lda];
+        if (d == 0.0) d = 1e-300;
+        X[i][j] = s / d;
+      }
+    }
+  }
+  __syncthreads();
+  double* D = t.dinv + (size_t)(upper * t.nblk + b) * GETRS_PANEL * GETRS_PANEL;
+  for (int i = 0; i < GETRS_PANEL; i++) D[i + j * GETRS_PANEL] = X[i][j];
+}
+
+// Panel solve.  w1 = P B, then for every panel of GETRS_PANEL columns a
+// launch over (row chunks, tasks): each CTA solves the panel's diagonal block
+// (one warp, rows in registers, values by shuffle) from `in` and updates its
+// chunk of the remaining rows of `in` in place; CTA 0 of a task writes the
+// diagonal block's solution to `out`.  Forward: in = w1, out = w2 (unit lower
+// L); backward: in = w2, out = B (upper U).  Within a launch the diagonal rows
+// of `in` are only read and every other row has one writer.
+__global__ void k_getrs_gather(const RsPanel* __restrict__ tasks) {
+  const RsPanel t = tasks[blockIdx.y];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= t.n) return;
+  const int src = t.perm[i];
+  for (int c = 0; c < t.ncols; c++) t.w1[i + (long long)c * t.n] = t.B[src + (long long)c * t.ldb];
+}
+
+__device__ inline const double* LU_row(const double* LU, int i, int k0, long long lda) {
+  return LU + i + k0 * lda;
+}
+
+__global__ void __launch_bounds__(GETRS_PROWS) k_getrs_panel(const RsPanel* __restrict__ tasks,
+                                                            int k0, int upper) {
+  const RsPanel t = tasks[blockIdx.y];
+  const int n = t.n;
+  if (k0 >= n) return;
+  const int jb = min(GETRS_PANEL, n - k0);
+  const int r_lo = upper ? 0 : k0 + jb, r_hi = upper ? k0 : n;  // rows to update
+  if (blockIdx.x > 0 && r_lo + blockIdx.x * GETRS_PROWS >= r_hi) return;
+  const int i = r_lo + blockIdx.x * GETRS_PROWS + threadIdx.x;
+  const long long lda = t.lda;
+  const double* D = t.dinv + (size_t)(upper * t.nblk + k0 / GETRS_PANEL) * GETRS_PANEL * GETRS_PANEL;
+  __shared__ double xin[GETRS_PANEL];
+  __shared__ double half[2][GETRS_PANEL];
+  __shared__ double xd[GETRS_PANEL];
+  const int r = threadIdx.x & (GETRS_PANEL - 1), h = threadIdx.x / GETRS_PANEL;
+  for (int c = 0; c < t.ncols; c++) {
+    double* in = (upper ? t.w2 : t.w1) + (long long)c * n;
+    double* out = upper ? t.B + (long long)c * t.ldb : t.w2 + (long long)c * n;
+    if (threadIdx.x < GETRS_PANEL) xin[threadIdx.x] = threadIdx.x < jb ? in[k0 + threadIdx.x] : 0.0;
+    __syncthreads();
+    {  // xd = D xin: thread (r, h) sums 32 columns in four chains
+      const double* d = D + r + (size_t)(h * 32) * GETRS_PANEL;
+      const double* x = xin + h * 32;
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+#pragma unroll
+      for (int q = 0; q < 32; q += 4) {
+        s0 = fma(d[(q + 0) * GETRS_PANEL], x[q + 0], s0);
+        s1 = fma(d[(q + 1) * GETRS_PANEL], x[q + 1], s1);
+        s2 = fma(d[(q + 2) * GETRS_PANEL], x[q + 2], s2);
+        s3 = fma(d[(q + 3) * GETRS_PANEL], x[q + 3], s3);
+      }
+      half[h][r] = (s0 + s1) + (s2 + s3);
+    }
+    __syncthreads();
+    if (threadIdx.x < GETRS_PANEL) xd[threadIdx.x] = half[0][threadIdx.x] + half[1][threadIdx.x];
+    __syncthreads();
+    if (blockIdx.x == 0)
+      for (int q = threadIdx.x; q < jb; q += blockDim.x) out[k0 + q] = xd[q];
+    if (i < r_hi) {
+      const double* a = LU_row(t.LU, i, k0, lda);
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      if (jb == GETRS_PANEL) {
+#pragma unroll
+        for (int q = 0; q < GETRS_PANEL; q += 4) {
+          s0 = fma(a[(q + 0) * lda], xd[q + 0], s0);
+          s1 = fma(a[(q + 1) * lda], xd[q + 1], s1);
+          s2 = fma(a[(q + 2) * lda], xd[q + 2], s2);
+          s3 = fma(a[(q + 3) * lda], xd[q + 3], s3);
+        }
+      } else {
+        for (int q = 0; q < jb; q++) s0 = fma(a[q * lda], xd[q], s0);
+      }
+      in[i] -= (s0 + s1) + (s2 + s3);
+    }
+    __syncthreads();
+  }
+}
+
 GemmLaunch plan_gemms(Arena& ar, const std::vector<GemmTask>& tasks, cudaStream_t s) {
   GemmLaunch L;
   std::vector<GemmTask> kept;
@@ -514,6 +642,29 @@ GetrsPlan plan_getrs(Arena& ar, const std::vector<RsTask>& tasks, cudaStream_t s
   int cmax = 0;
   for (auto& t : tasks) { P.nmax = std::max(P.nmax, t.n); cmax = std::max(cmax, t.ncols); }
   if (P.nmax == 0 || cmax == 0) { P.nt = 0; return P; }
+  if (cmax <= GETRS_SMALL_COLS) {
+    std::vector<int*> pm(tasks.size());
+    for (size_t i = 0; i < tasks.size(); i++) pm[i] = ar.alloc<int>(std::max(tasks[i].n, 1));
+    const int* const* dpm = upload(ar, pm, s);
+    k_piv_to_perm<<<(P.nt + 127) / 128, 128, 0, s>>>(P.d, const_cast<int* const*>(dpm), P.nt);
+    CK_LAUNCH("k_piv_to_perm");
+    P.panel = true;
+    std::vector<RsPanel> pt;
+    for (size_t i = 0; i < tasks.size(); i++) {
+      const RsTask& t = tasks[i];
+      const size_t len = (size_t)std::max(t.n, 1) * std::max(t.ncols, 1);
+      const int nblk = (t.n + GETRS_PANEL - 1) / GETRS_PANEL;
+      P.nblk_max = std::max(P.nblk_max, nblk);
+      pt.push_back({t.LU, t.lda, t.n, pm[i], t.B, t.ldb, t.ncols, ar.alloc<double>(len),
+                    ar.alloc<double>(len),
+                    ar.alloc<double>((size_t)2 * std::max(nblk, 1) * GETRS_PANEL * GETRS_PANEL),
+                    nblk});
+    }
+    P.pd = upload(ar, pt, s);
+    k_getrs_dinv<<<dim3(P.nblk_max, P.nt, 2), GETRS_PANEL, 0, s>>>(P.pd);
+    CK_LAUNCH("k_getrs_dinv");
+    return P;
+  }
   P.gy = std::min(64, (cmax + 127) / 128);
   for (int k0 = 0; k0 < P.nmax; k0 += LU_NB) {
     std::vector<GemmTask> g;
@@ -543,6 +694,22 @@ GetrsPlan plan_getrs(Arena& ar, const std::vector<RsTask>& tasks, cudaStream_t s
 
 void exec_getrs(const GetrsPlan& P, cudaStream_t s) {
   if (P.nt == 0) return;
+  if (P.panel) {
+    Prof pr("phase:getrs_panel", 2.0 * P.nmax * (double)P.nmax * P.nt, 8.0 * P.nmax * (double)P.nmax * P.nt, s);
+    k_getrs_gather<<<dim3((P.nmax + 255) / 256, P.nt), 256, 0, s>>>(P.pd);
+    CK_LAUNCH("k_getrs_gather");
+    const dim3 grid((P.nmax + GETRS_PROWS - 1) / GETRS_PROWS, P.nt);
+    for (int k0 = 0; k0 < P.nmax; k0 += GETRS_PANEL) {
+      k_getrs_panel<<<grid, GETRS_PROWS, 0, s>>>(P.pd, k0, 0);
+      CK_LAUNCH("k_getrs_panel");
+    }
+    for (int k0 = ((P.nmax - 1) / GETRS_PANEL) * GETRS_PANEL; k0 >= 0; k0 -= GETRS_PANEL) {
+      k_getrs_panel<<<grid, GETRS_PROWS, 0, s>>>(P.pd, k0, 1);
+      CK_LAUNCH("k_getrs_panel");
+    }
+    return;
+  }
+  Prof pr("phase:getrs_blocked", 2.0 * P.nmax * (double)P.nmax * P.nt, 8.0 * P.nmax * (double)P.nmax * P.nt, s);
   k_laswp_rhs<<<dim3(P.nt, P.gy), 128, 0, s>>>(P.d);
   CK_LAUNCH("k_laswp_rhs");
   int step = 0;
@@ -568,151 +735,260 @@ void run_getrs(Arena& ar, const std::vector<RsTask>& tasks, cudaStream_t s) {
 
 // ---------------------------------------------------------------------------
 // Left SVD: streaming LQ (M = L Q^T) then one-sided Jacobi on the columns of
-// L (L J = W Sigma).  The LQ keeps L (a x a, lower) and a chunk C of CW
-// columns of M side by side, [L | C], and annihilates C row by row with
-// Householder reflectors; after the last chunk L carries the left singular
-// structure of M.  Both phases live in shared memory when a <= SVD_SMEM_A,
-// otherwise in the task's global scratch.
+// L (L J = W Sigma).  The LQ keeps L (a x a, lower) and a chunk C of columns
+// of M side by side, [L | C], and annihilates C row by row with Householder
+// reflectors; after the last chunk L carries the left singular structure of
+// M.  Both phases live in shared memory when a <= SVD_SMEM_A, otherwise in
+// global scratch.
+//
+// FP64 throughput is the limit on this part (a few FP64 lanes per SM per
+// clock), so the kernels spend FP64 instructions only on the arithmetic:
+// G lanes share one row (LQ) or one column pair (Jacobi) so that a warp
+// instruction carries 32 / G rows or pairs, reductions take log2(G) adds, the
+// reflector and rotation scalars are formed once per row or pair, rotations
+// are scaled (two FMAs per element, column scales kept aside) and the column
+// norms are carried through each rotation instead of being recomputed.
 // ---------------------------------------------------------------------------
-constexpr int SVD_SMEM_A = 144;
-constexpr int SVD_CW = 16;
+constexpr int SVD_CW = 16;  // chunk width of the global-memory path
 
 struct SvdView {
   double* L;    // a x a, ld = lda
-  double* C;    // a x CW, ld = ldc
+  double* C;    // a x cw, ld = ldc
   int lda, ldc;
 };
 
-// Annihilate chunk columns [0, cw) of C against L (rows 0..a-1).
-__device__ void lq_chunk(SvdView v, int a, int cw, double* red, double* vsh) {
+// H = I - beta v v^T with v = [v0, C[k, :]] (v0 on L[k, k]); the row
+// [L[k, k], C[k, :]] maps to [alpha, 0]; beta = 2 / (v^T v) = -1 / (alpha v0).
+struct Refl { double alpha, v0, beta; };
+
+template <int G>
+__device__ inline double group_sum(double v) {
+#pragma unroll
+  for (int o = 1; o < G; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ inline Refl make_refl(double x0, double sq) {
+  Refl r;
+  if (sq == 0.0) {  // nothing to annihilate: identity (beta = 0)
+    r.alpha = x0; r.v0 = 0.0; r.beta = 0.0;
+    return r;
+  }
+  const double nrm = sqrt(fma(x0, x0, sq));
+  r.alpha = (x0 >= 0.0) ? -nrm : nrm;
+  r.v0 = x0 - r.alpha;  // same sign as x0: no cancellation
+  r.beta = -1.0 / (r.alpha * r.v0);
+  return r;
+}
+
+// Annihilate the chunk C (a x cw) against L, rows 0..a-1 in order.  The group
+// that updates row k + 1 during step k also forms that row's reflector, so a
+// step costs one barrier; refl[2] alternates between steps.
+template <int G>
+__device__ void lq_chunk(SvdView v, int a, int cw, Refl* refl) {
+  constexpr int RPW = 32 / G;  // rows per warp instruction
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int k = 0; k < a; k++) {
-    // reflector from (L[k,k], C[k, 0..cw))
+  const int grp = lane / G, q = lane % G;
+  if (wid == 0) {
     double sq = 0.0;
-    for (int c = threadIdx.x; c < cw; c += blockDim.x) {
-      const double x = v.C[k + c * v.ldc];
-      sq += x * x;
+    for (int c = lane; c < cw; c += 32) {
+      const double x = v.C[(size_t)c * v.ldc];
+      sq = fma(x, x, sq);
     }
-    sq = block_sum(sq, red);
-    const double x0 = v.L[k + k * v.lda];
-    if (sq == 0.0) continue;                    // nothing to annihilate (block-uniform)
-    const double nrm = sqrt(x0 * x0 + sq);
-    const double alpha = (x0 >= 0.0) ? -nrm : nrm;
-    const double v0 = x0 - alpha;               // v = [v0, C[k, :]], H = I - tau v v^T
-    const double tau = -v0 / alpha;             // = (alpha - x0) / alpha
-    const double scale = 1.0 / v0;
-    // normalised reflector: u = [1, C[k,:]/v0], H = I - tau u u^T
-    for (int c = threadIdx.x; c < cw; c += blockDim.x) vsh[c] = v.C[k + c * v.ldc] * scale;
-    __syncthreads();
-    for (int i = k + 1 + wid; i < a; i += nw) {
+    sq = warp_sum(sq);
+    if (lane == 0) refl[0] = make_refl(v.L[0], sq);
+  }
+  __syncthreads();
+  for (int k = 0; k < a; k++) {
+    const Refl R = refl[k & 1];
+    const double* ck = v.C + k;
+    for (int base = k + 1 + wid * RPW; base < a; base += nw * RPW) {  // warp-uniform
+      const int i = base + grp;
+      const bool act = i < a;
+      const bool next = (base == k + 1);  // this pass holds row k + 1 (group 0)
+      double* ci = v.C + i;
+      double* li = v.L + i + (size_t)k * v.lda;
       double d = 0.0;
-      for (int c = lane; c < cw; c += 32) d += v.C[i + c * v.ldc] * vsh[c];
-      d = warp_sum(d) + v.L[i + k * v.lda];
-      const double f = tau * d;
-      for (int c = lane; c < cw; c += 32) v.C[i + c * v.ldc] -= f * vsh[c];
-      if (lane == 0) v.L[i + k * v.lda] -= f;
+      if (act) {
+        for (int c = q; c < cw; c += G) d = fma(ci[(size_t)c * v.ldc], ck[(size_t)c * v.ldc], d);
+        if (q == 0) d = fma(*li, R.v0, d);
+      }
+      d = group_sum<G>(d);
+      double sq = 0.0;
+      if (act) {
+        const double f = R.beta * d;
+        for (int c = q; c < cw; c += G) {
+          const double x = fma(-f, ck[(size_t)c * v.ldc], ci[(size_t)c * v.ldc]);
+          ci[(size_t)c * v.ldc] = x;
+          if (next) sq = fma(x, x, sq);
+        }
+        if (q == 0) *li = fma(-f, R.v0, *li);
+      }
+      if (next) {
+        sq = group_sum<G>(sq);
+        if (lane == 0) refl[(k + 1) & 1] = make_refl(v.L[(k + 1) + (size_t)(k + 1) * v.lda], sq);
+      }
     }
-    __syncthreads();
-    if (threadIdx.x == 0) v.L[k + k * v.lda] = alpha;
-    for (int c = threadIdx.x; c < cw; c += blockDim.x) v.C[k + c * v.ldc] = 0.0;
+    if (threadIdx.x == 0) v.L[k + (size_t)k * v.lda] = R.alpha;
     __syncthreads();
   }
 }
 
-__device__ void jacobi_columns(double* L, int lda, int a, double* red) {
-  // round-robin pairing over n = a rounded up to even; a warp per pair
+// Squared column norms of L (a x a) into nr, folding the column scales dsc
+// into the data first when `fold` is set; scales reset to one.
+template <int G>
+__device__ void jacobi_norms(double* L, int lda, int a, double* nr, double* dsc, double* dinv,
+                             bool fold) {
+  constexpr int PPW = 32 / G;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int grp = lane / G, q = lane % G;
+  for (int base = wid * PPW; base < a; base += nw * PPW) {  // warp-uniform
+    const int j = base + grp;
+    const bool act = j < a;
+    double s = 0.0;
+    if (act) {
+      const double dj = fold ? dsc[j] : 1.0;
+      double* x = L + (size_t)j * lda;
+      for (int r = q; r < a; r += G) {
+        double e = x[r];
+        if (fold) { e *= dj; x[r] = e; }
+        s = fma(e, e, s);
+      }
+    }
+    s = group_sum<G>(s);
+    if (act && q == 0) { nr[j] = s; dsc[j] = 1.0; dinv[j] = 1.0; }
+  }
+}
+
+// One-sided Jacobi on the columns of L (a x a, ld lda), round-robin pairing;
+// on return L = W Sigma (columns orthogonal).  Column j is stored as X_j with
+// the true column dsc[j] X_j; a rotation of (p, q) with tangent t becomes
+// X_p -= t (d_q / d_p) X_q, X_q += t (d_p / d_q) X_p, d_p, d_q *= cos.
+// nr carries the true squared norms (||x_p||^2 -= t g, ||x_q||^2 += t g).
+template <int G>
+__device__ void jacobi_columns(double* L, int lda, int a, double* nr, double* dsc, double* dinv,
+                               int* flag) {
+  constexpr int PPW = 32 / G;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int grp = lane / G, q = lane % G;
   const int n = (a + 1) & ~1;
-  __shared__ int rotated;
   for (int sweep = 0; sweep < 40; sweep++) {
-    if (threadIdx.x == 0) rotated = 0;
+    jacobi_norms<G>(L, lda, a, nr, dsc, dinv, sweep > 0);
+    if (threadIdx.x == 0) *flag = 0;
     __syncthreads();
     for (int round = 0; round < n - 1; round++) {
-      for (int pr = wid; pr < n / 2; pr += nw) {
+      for (int base = wid * PPW; base < n / 2; base += nw * PPW) {  // warp-uniform
         // round-robin tournament: seat 0 fixed, seats 1..n-1 rotate by `round`;
         // seat m plays seat n-1-m, so every pair meets once per sweep
-        const int ma = pr, mb = n - 1 - pr;
-        const int pa = (ma == 0) ? 0 : ((ma - 1 + round) % (n - 1)) + 1;
-        const int pb = (mb == 0) ? 0 : ((mb - 1 + round) % (n - 1)) + 1;
-        const int p = min(pa, pb), q = max(pa, pb);
-        if (q >= a || p == q) continue;
-        double al = 0.0, be = 0.0, ga = 0.0;
-        for (int r = lane; r < a; r += 32) {
-          const double x = L[r + p * lda], y = L[r + q * lda];
-          al += x * x; be += y * y; ga += x * y;
+        const int pr = base + grp;
+        int p = 0, r2 = 0;
+        bool act = pr < n / 2;
+        if (act) {
+          const int ma = pr, mb = n - 1 - pr;
+          const int pa = (ma == 0) ? 0 : ((ma - 1 + round) % (n - 1)) + 1;
+          const int pb = (mb == 0) ? 0 : ((mb - 1 + round) % (n - 1)) + 1;
+          p = min(pa, pb);
+          r2 = max(pa, pb);
+          act = (r2 < a) && (p != r2);
         }
-        al = warp_sum(al); be = warp_sum(be); ga = warp_sum(ga);
-        if (fabs(ga) > 1e-15 * sqrt(al * be) && ga != 0.0) {
-          const double zeta = (be - al) / (2.0 * ga);
-          const double tt = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          const double cs = 1.0 / sqrt(1.0 + tt * tt), sn = cs * tt;
-          for (int r = lane; r < a; r += 32) {
-            const double x = L[r + p * lda], y = L[r + q * lda];
-            L[r + p * lda] = cs * x - sn * y;
-            L[r + q * lda] = sn * x + cs * y;
+        double* xp = L + (size_t)p * lda;
+        double* xq = L + (size_t)r2 * lda;
+        double g = 0.0, dp = 1.0, dq = 1.0, ip = 1.0, iq = 1.0, al = 0.0, be = 0.0;
+        if (act) {
+          for (int r = q; r < a; r += G) g = fma(xp[r], xq[r], g);
+          dp = dsc[p]; dq = dsc[r2]; ip = dinv[p]; iq = dinv[r2]; al = nr[p]; be = nr[r2];
+        }
+        g = group_sum<G>(g);  // identical in every lane of the group
+        if (act) {
+          g *= dp * dq;
+          if (g != 0.0 && g * g > 1e-30 * (al * be)) {
+            // t = tan(theta), the smaller root of t^2 + 2 zeta t - 1 = 0 with
+            // zeta = (be - al) / (2 g), written without the division by g
+            const double del = be - al;
+            const double h = sqrt(fma(del, del, 4.0 * g * g));
+            const double t = (del >= 0.0 ? 2.0 * g : -2.0 * g) / (fabs(del) + h);
+            const double tt1 = fma(t, t, 1.0);
+            const double c = rsqrt(tt1);
+            const double t1 = t * dq * ip, t2 = t * dp * iq;
+            for (int r = q; r < a; r += G) {
+              const double x = xp[r], y = xq[r];
+              xp[r] = fma(-t1, y, x);
+              xq[r] = fma(t2, x, y);
+            }
+            if (q == 0) {
+              const double ic = tt1 * c;  // 1 / cos
+              dsc[p] = dp * c;
+              dsc[r2] = dq * c;
+              dinv[p] = ip * ic;
+              dinv[r2] = iq * ic;
+              nr[p] = fmax(fma(-t, g, al), 0.0);
+              nr[r2] = fma(t, g, be);
+              *flag = 1;
+            }
           }
-          if (lane == 0) rotated = 1;
         }
       }
       __syncthreads();
+      if ((round & 63) == 63 && round + 1 < n - 1) {
+        // long sweeps: fold the scales back before they drift far from one
+        jacobi_norms<G>(L, lda, a, nr, dsc, dinv, true);
+        __syncthreads();
+      }
     }
+    const bool again = *flag != 0;
     __syncthreads();
-    if (!rotated) break;
-    __syncthreads();
+    if (!again) break;
   }
+  jacobi_norms<G>(L, lda, a, nr, dsc, dinv, true);
+  __syncthreads();
 }
 
-// cw: columns streamed per chunk (shared-memory mode); the reflector vector
-// lives behind the chunk in dynamic shared memory.
-__global__ void __launch_bounds__(1024) k_svd_left(const SvdTask* __restrict__ tasks, int use_smem,
-                                                   int cw_max) {
+template <int G>
+__global__ void __launch_bounds__(512) k_svd_left(const SvdTask* __restrict__ tasks, int use_smem,
+                                                  int cw_max) {
   const SvdTask t = tasks[blockIdx.x];
   const int a = t.a;
   if (a <= 0) return;
   if ((a <= SVD_SMEM_A) != (use_smem != 0)) return;
   extern __shared__ double sm[];
-  __shared__ double red[40];
-  __shared__ double vsh_g[SVD_CW];
+  __shared__ Refl refl[2];
+  __shared__ int flag;
   SvdView v;
-  double* vsh;
+  double* aux;  // nr, dsc, dinv: 3a doubles
   int cwm;
   if (use_smem) {
     v.L = sm;
     v.lda = a + 1;                 // odd stride: no bank conflicts on row access
     v.C = sm + (size_t)(a + 1) * a;
     v.ldc = a + 1;
-    vsh = v.C + (size_t)(a + 1) * cw_max;
+    aux = v.C + (size_t)(a + 1) * cw_max;
     cwm = cw_max;
   } else {
     v.L = t.work;
     v.lda = a;
     v.C = t.work + (size_t)a * a;
     v.ldc = a;
-    vsh = vsh_g;
+    aux = sm;
     cwm = SVD_CW;
   }
   // L starts at zero; every column of M is streamed through the chunk C and
   // annihilated against L (the reflector treats L[k,k] as its first entry).
-  for (int e = threadIdx.x; e < a * a; e += blockDim.x) v.L[(e % a) + (e / a) * v.lda] = 0.0;
+  for (int e = threadIdx.x; e < a * a; e += blockDim.x) v.L[(e % a) + (size_t)(e / a) * v.lda] = 0.0;
   __syncthreads();
   for (int c0 = 0; c0 < t.w; c0 += cwm) {
     const int cw = min(cwm, t.w - c0);
     for (int e = threadIdx.x; e < a * cw; e += blockDim.x) {
       const int r = e % a, c = e / a;
-      v.C[r + c * v.ldc] = t.M[r + (long long)(c0 + c) * t.ldm];
+      v.C[r + (size_t)c * v.ldc] = t.M[r + (long long)(c0 + c) * t.ldm];
     }
     __syncthreads();
-    lq_chunk(v, a, cw, red, vsh);
+    lq_chunk<G>(v, a, cw, refl);
   }
-  jacobi_columns(v.L, v.lda, a, red);
+  jacobi_columns<G>(v.L, v.lda, a, aux, aux + a, aux + 2 * a, &flag);
   // sigma_j = |L_j|; order by decreasing sigma (ties: lower column first).
   // The chunk area (>= a doubles) is free now and holds the column norms.
   double* sg = v.C;
-  for (int j = threadIdx.x; j < a; j += blockDim.x) {
-    double s = 0.0;
-    for (int r = 0; r < a; r++) { const double x = v.L[r + j * v.lda]; s += x * x; }
-    sg[j] = sqrt(s);
-  }
+  for (int j = threadIdx.x; j < a; j += blockDim.x) sg[j] = sqrt(aux[j]);
   __syncthreads();
   double smax = 0.0;
   for (int j = 0; j < a; j++) smax = fmax(smax, sg[j]);
@@ -721,11 +997,14 @@ __global__ void __launch_bounds__(1024) k_svd_left(const SvdTask* __restrict__ t
     for (int k = 0; k < a; k++) pos += (sg[k] > sg[j]) || (sg[k] == sg[j] && k < j);
     t.sigma[pos] = sg[j];
     const double inv = sg[j] > 0.0 ? 1.0 / sg[j] : 0.0;
-    for (int r = 0; r < a; r++) t.W[r + (long long)pos * a] = v.L[r + j * v.lda] * inv;
+    for (int r = 0; r < a; r++) t.W[r + (long long)pos * a] = v.L[r + (size_t)j * v.lda] * inv;
   }
   __syncthreads();
   // complete the basis where sigma is negligible: Gram-Schmidt (twice) against
   // the preceding columns, starting from the column or from unit vectors
+  double* red = aux;  // the Jacobi scratch is free now (>= 3a >= 33 doubles for a >= 11)
+  __shared__ double red_small[40];
+  if (3 * a < 40) red = red_small;
   const double small = smax * 1e-13 * a + 1e-300;
   for (int j = 0; j < a; j++) {
     if (t.sigma[j] > small) continue;
@@ -767,15 +1046,18 @@ static bool svd_tracing() {
   return v;
 }
 
-void run_svd_left(Arena& ar, const std::vector<SvdTask>& tasks, cudaStream_t s) {
-  if (tasks.empty()) return;
+void run_svd_left(Arena& ar, const std::vector<SvdTask>& tasks_in, cudaStream_t s) {
+  if (tasks_in.empty()) return;
   std::chrono::steady_clock::time_point t0;
   if (svd_tracing()) {
     CK(cudaStreamSynchronize(s));
     t0 = std::chrono::steady_clock::now();
   }
+  std::vector<SvdTask> tasks(tasks_in);
   for (auto& t : tasks) {
     if (t.a <= 0) continue;
+    if (t.a > SVD_SMEM_A && !t.work)
+      t.work = ar.alloc<double>((size_t)t.a * t.a + (size_t)t.a * SVD_CW);
     Ranges::check(t.M, mat_bytes(t.a, t.w, t.ldm), "svd M");
     Ranges::check(t.W, mat_bytes(t.a, t.a, t.a), "svd W");
     Ranges::check(t.sigma, sizeof(double) * t.a, "svd sigma");
@@ -783,46 +1065,54 @@ void run_svd_left(Arena& ar, const std::vector<SvdTask>& tasks, cudaStream_t s) 
       Ranges::check(t.work, sizeof(double) * ((size_t)t.a * t.a + (size_t)t.a * SVD_CW), "svd work");
   }
   const SvdTask* d = upload(ar, tasks, s);
-  int amax_s = 0;
-  bool big = false;
+  int amax_s = 0, amax_g = 0, wmax = 0;
   for (auto& t : tasks) {
-    if (t.a <= SVD_SMEM_A) amax_s = std::max(amax_s, t.a);
-    else big = true;
+    if (t.a <= SVD_SMEM_A) {
+      amax_s = std::max(amax_s, t.a);
+      wmax = std::max(wmax, t.w);
+    } else {
+      amax_g = std::max(amax_g, t.a);
+    }
   }
   double fl = 0.0;
   for (auto& t : tasks) fl += 2.0 * t.a * (double)t.a * t.w;
   Prof p("k_svd_left", fl, 0.0, s);
+  static bool attr = false;
+  if (!attr) {
+    CK(cudaFuncSetAttribute(k_svd_left<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            SVD_SMEM_BUDGET * 8));
+    CK(cudaFuncSetAttribute(k_svd_left<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            SVD_SMEM_BUDGET * 8));
+    attr = true;
+  }
   if (amax_s > 0) {
-    // widest chunk that fits next to L: (a+1)(a+cw) + cw doubles <= 200 KiB
-    const long long budget = (200 * 1024) / 8;
-    long long cw = (budget - (long long)(amax_s + 1) * amax_s) / (amax_s + 2);
-    int wmax = 0;
-    for (auto& t : tasks) if (t.a <= SVD_SMEM_A) wmax = std::max(wmax, t.w);
-    cw = std::min<long long>(cw, 2048);
+    // shared memory: L ((a+1) x a), chunk ((a+1) x cw), 3a doubles of Jacobi
+    // state.  Small blocks take a smaller budget so several CTAs share an SM.
+    const long long a = amax_s;
+    const long long budget = a <= 32 ? SVD_SMEM_BUDGET / 4 : (a <= 80 ? SVD_SMEM_BUDGET / 2
+                                                                        : SVD_SMEM_BUDGET);
+    long long cw = (budget - (a + 1) * a - 3 * a) / (a + 1);
     cw = std::min<long long>(cw, std::max(wmax, 1));
-    cw = std::max<long long>(cw, SVD_CW);
-    const size_t smem = sizeof(double) * ((size_t)(amax_s + 1) * (amax_s + cw) + cw);
-    static bool attr = false;
-    if (!attr) {
-      CK(cudaFuncSetAttribute(k_svd_left, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              200 * 1024));
-      attr = true;
+    if (cw < 1) throw Error(IFMM_ERR_CUDA, "internal: SVD shared-memory budget too small");
+    const size_t smem = sizeof(double) * (size_t)((a + 1) * (a + cw) + 3 * a);
+    if (a <= 32) {
+      k_svd_left<4><<<(int)tasks.size(), 128, smem, s>>>(d, 1, (int)cw);
+    } else {
+      k_svd_left<8><<<(int)tasks.size(), a <= 64 ? 256 : 512, smem, s>>>(d, 1, (int)cw);
     }
-    const int threads = amax_s > 96 ? 512 : 256;
-    k_svd_left<<<(int)tasks.size(), threads, smem, s>>>(d, 1, (int)cw);
     CK_LAUNCH("k_svd_left(smem)");
   }
-  if (big) {
-    k_svd_left<<<(int)tasks.size(), 512, 0, s>>>(d, 0, SVD_CW);
+  if (amax_g > 0) {
+    k_svd_left<8><<<(int)tasks.size(), 512, sizeof(double) * 3 * (size_t)amax_g, s>>>(d, 0, SVD_CW);
     CK_LAUNCH("k_svd_left(global)");
   }
   if (svd_tracing()) {
     CK(cudaStreamSynchronize(s));
-    int amax = 0, wmax = 0;
+    int amax = 0, wm = 0;
     double wsum = 0.0;
-    for (auto& t : tasks) { amax = std::max(amax, t.a); wmax = std::max(wmax, t.w); wsum += t.w; }
+    for (auto& t : tasks) { amax = std::max(amax, t.a); wm = std::max(wm, t.w); wsum += t.w; }
     std::fprintf(stderr, "[svd] tasks %zu, max a %d, max w %d, avg w %.0f, %.4f s\n", tasks.size(),
-                 amax, wmax, wsum / tasks.size(),
+                 amax, wm, wsum / tasks.size(),
                  std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
   }
 }
@@ -926,8 +1216,8 @@ void run_rsvd_left(Arena& ar, const std::vector<RsvdTask>& tasks, cudaStream_t s
   // tasks are grouped by k (all tasks of one call share k)
   const int k = tasks[0].k;
   for (auto& t : tasks)
-    if (t.k != k || t.k > SVD_SMEM_A || t.k > t.a)
-      throw Error(IFMM_ERR_CUDA, "internal: randomised SVD tasks need a common k <= 144 <= a");
+    if (t.k != k || t.k > SVD_EXACT_MAX_A || t.k > t.a)
+      throw Error(IFMM_ERR_CUDA, "internal: randomised SVD tasks need a common k <= 144, k <= a");
   std::vector<double*> Om(nt), Y(nt), Q(nt), Z(nt), Qz(nt), B(nt), WB(nt);
   std::vector<GemmTask> g;
   for (int t = 0; t < nt; t++) {

@@ -152,30 +152,180 @@ __global__ void __launch_bounds__(256) k_direct(KSpec ks, int dim, const double*
   if (i < N) y[(long long)col * ldy + i] = acc;
 }
 
-// block-row sparse product: one CTA per output row-block
-__global__ void __launch_bounds__(128) k_spmm(const SpRow* __restrict__ rows,
-                                              const SpEnt* __restrict__ ents, int nrhs) {
-  const SpRow R = rows[blockIdx.x];
-  for (int c = 0; c < nrhs; c++) {
-    for (int r = threadIdx.x; r < R.m; r += blockDim.x) {
+// Block-row sparse product, one CTA per job (SpJob): 32 rows at a time, the
+// 8 warps take interleaved columns of each non-transposed segment (coalesced
+// 256-byte column pieces of A, one FMA per element); transposed segments go a
+// row per warp with the lanes along the column.  Per-warp sums meet in shared
+// memory in a fixed order.
+constexpr int SPMM_WARPS = 8;
+
+__device__ inline double warp_sum_d(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(256) k_spmm_job(const SpRow* __restrict__ rows,
+                                                  const SpEnt* __restrict__ ents,
+                                                  const SpJob* __restrict__ jobs,
+                                                  const SpSeg* __restrict__ segs,
+                                                  double* __restrict__ part, long long pld,
+                                                  int c0, int nb) {
+  const SpJob J = jobs[blockIdx.x];
+  const SpRow R = rows[J.row];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __shared__ double sacc[SPMM_WARPS][33];
+  __shared__ double sacc_t[32];
+  for (int c = 0; c < nb; c++) {
+    for (int rt = 0; rt < R.m; rt += 32) {
+      const int r = rt + lane;
+      const bool rin = r < R.m;
+      if (threadIdx.x < 32) sacc_t[threadIdx.x] = 0.0;
+      __syncthreads();
       double acc = 0.0;
-      for (int e = R.e0; e < R.e0 + R.ne; e++) {
-        const SpEnt E = ents[e];
-        const double* x = E.x + (long long)c * E.ldx;
-        double s = 0.0;
-        if (!E.A) {
-          s = x[r];
+      for (int si = J.s0; si < J.s0 + J.ns; si++) {
+        const SpSeg G = segs[si];
+        const SpEnt E = ents[G.ent];
+        const double* x = E.x + (long long)(c0 + c) * E.ldx;
+        if (!E.A) {  // identity: rows k0..k1 of this entry
+          if (wid == 0 && rin && r >= G.k0 && r < G.k1) acc = fma(E.alpha, x[r], acc);
         } else if (!E.transA) {
-          const double* a = E.A + r;
-          for (int q = 0; q < E.k; q++) s += a[(long long)q * E.lda] * x[q];
-        } else {
-          const double* a = E.A + (long long)r * E.lda;
-          for (int q = 0; q < E.k; q++) s += a[q] * x[q];
+          if (rin) {
+            const double* a = E.A + r;
+            double s0 = 0.0, s1 = 0.0;
+            int col = G.k0 + wid;
+            for (; col + SPMM_WARPS < G.k1; col += 2 * SPMM_WARPS) {
+              s0 = fma(a[(long long)col * E.lda], x[col], s0);
+              s1 = fma(a[(long long)(col + SPMM_WARPS) * E.lda], x[col + SPMM_WARPS], s1);
+            }
+            if (col < G.k1) s0 = fma(a[(long long)col * E.lda], x[col], s0);
+            acc = fma(E.alpha, s0 + s1, acc);
+          }
+        } else {  // op(A) = A^T with A (k x m): output row r is column r of A
+          const int rmax = min(32, R.m - rt);
+          for (int rl = wid; rl < rmax; rl += SPMM_WARPS) {  // warp-uniform
+            const double* a = E.A + (long long)(rt + rl) * E.lda;
+            double d = 0.0;
+            for (int col = G.k0 + lane; col < G.k1; col += 32) d = fma(a[col], x[col], d);
+            d = warp_sum_d(d);
+            if (lane == 0) sacc_t[rl] = fma(E.alpha, d, sacc_t[rl]);
+          }
         }
-        acc += E.alpha * s;
       }
-      double* y = R.y + (long long)c * R.ldy + r;
-      *y = (R.beta == 0.0) ? acc : R.beta * (*y) + acc;
+      sacc[wid][lane] = acc;
+      __syncthreads();
+      if (wid == 0 && rin) {
+        double v = sacc_t[lane];
+#pragma unroll
+        for (int w = 0; w < SPMM_WARPS; w++) v += sacc[w][lane];
+        if (J.part < 0) {
+          double* y = R.y + (long long)(c0 + c) * R.ldy + r;
+          *y = (R.beta == 0.0) ? v : fma(R.beta, *y, v);
+        } else {
+          part[J.part + r + (long long)c * pld] = v;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// y = beta y + (sum of the row's partial sums, in job order)
+__global__ void __launch_bounds__(256) k_spmm_reduce(const SpRow* __restrict__ rows,
+                                                     const SpRed* __restrict__ reds,
+                                                     const double* __restrict__ part,
+                                                     long long pld, int c0, int nb) {
+  const SpRed D = reds[blockIdx.x];
+  const SpRow R = rows[D.row];
+  for (int c = 0; c < nb; c++)
+    for (int r = threadIdx.x; r < R.m; r += blockDim.x) {
+      const double* pp = part + D.base + r + (long long)c * pld;
+      double v = 0.0;
+      for (int j = 0; j < D.nj; j++) v += pp[(long long)j * R.m];
+      double* y = R.y + (long long)(c0 + c) * R.ldy + r;
+      *y = (R.beta == 0.0) ? v : fma(R.beta, *y, v);
+    }
+}
+
+SpmmPlan plan_spmm(Arena& ar, const std::vector<SpRow>& rows, const std::vector<SpEnt>& ents,
+                   int cap, cudaStream_t s) {
+  SpmmPlan P;
+  if (rows.empty()) return P;
+  if (cap < 1) cap = 1;
+  validate_spmm(rows, ents, cap);
+  int dev = 0, nsm = 1;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  double total = 0.0;
+  for (const SpRow& R : rows) {
+    P.bytes += 8.0 * R.m;
+    for (int e = R.e0; e < R.e0 + R.ne; e++) {
+      const SpEnt& E = ents[e];
+      P.flops += 2.0 * R.m * (double)E.k;
+      P.bytes += 8.0 * E.k + (E.A ? 8.0 * R.m * (double)E.k : 0.0);
+      total += (E.A ? (double)R.m : 1.0) * E.k;
+    }
+  }
+  // about four jobs per SM; no job below 8192 multiply-adds
+  const double target = std::max(8192.0, total / (4.0 * nsm));
+  std::vector<SpJob> jobs;
+  std::vector<SpSeg> segs;
+  std::vector<SpRed> reds;
+  long long poff = 0;
+  for (int ri = 0; ri < (int)rows.size(); ri++) {
+    const SpRow& R = rows[ri];
+    long long K = 0;
+    double work = 0.0;
+    for (int e = R.e0; e < R.e0 + R.ne; e++) {
+      K += ents[e].k;
+      work += (ents[e].A ? (double)R.m : 1.0) * ents[e].k;
+    }
+    int ns = (int)std::ceil(work / target);
+    if ((long long)ns > std::max(K, 1ll)) ns = (int)std::max(K, 1ll);
+    ns = std::max(1, std::min(ns, 64));
+    if (ns > 1) reds.push_back({ri, ns, poff});
+    for (int j = 0; j < ns; j++) {
+      const long long K0 = K * j / ns, K1 = K * (j + 1) / ns;
+      SpJob J{ri, (int)segs.size(), 0, ns > 1 ? poff + (long long)j * R.m : -1};
+      long long base = 0;
+      for (int e = R.e0; e < R.e0 + R.ne; e++) {
+        const long long lo = std::max(K0, base), hi = std::min(K1, base + ents[e].k);
+        if (lo < hi) {
+          segs.push_back({e, (int)(lo - base), (int)(hi - base)});
+          J.ns++;
+        }
+        base += ents[e].k;
+      }
+      jobs.push_back(J);
+    }
+    if (ns > 1) poff += (long long)ns * R.m;
+  }
+  P.rows = upload(ar, rows, s);
+  P.ents = upload(ar, ents, s);
+  P.jobs = upload(ar, jobs, s);
+  P.segs = segs.empty() ? nullptr : upload(ar, segs, s);
+  P.reds = reds.empty() ? nullptr : upload(ar, reds, s);
+  P.njobs = (int)jobs.size();
+  P.nreds = (int)reds.size();
+  P.part_ld = poff;
+  P.cap = cap;
+  if (poff > 0) P.part = ar.alloc<double>((size_t)poff * cap);
+  return P;
+}
+
+void launch_spmm(const SpmmPlan& p, int nrhs, cudaStream_t s) {
+  if (p.njobs <= 0 || nrhs <= 0) return;
+  for (int c0 = 0; c0 < nrhs; c0 += p.cap) {
+    const int nb = std::min(p.cap, nrhs - c0);
+    {
+      Prof pr("k_spmm_job", p.flops * nb, p.bytes * nb, s);
+      k_spmm_job<<<p.njobs, 256, 0, s>>>(p.rows, p.ents, p.jobs, p.segs, p.part, p.part_ld, c0,
+                                         nb);
+      CK_LAUNCH("k_spmm_job");
+    }
+    if (p.nreds > 0) {
+      Prof pr("k_spmm_reduce", 0.0, 16.0 * p.part_ld * nb, s);
+      k_spmm_reduce<<<p.nreds, 256, 0, s>>>(p.rows, p.reds, p.part, p.part_ld, c0, nb);
+      CK_LAUNCH("k_spmm_reduce");
     }
   }
 }
@@ -198,13 +348,6 @@ void validate_spmm(const std::vector<SpRow>& rows, const std::vector<SpEnt>& ent
   }
 }
 
-void launch_spmm(const SpRow* rows, int nrows, const SpEnt* ents, int nrhs, cudaStream_t s,
-                 double flops, double bytes) {
-  if (nrows <= 0 || nrhs <= 0) return;
-  Prof p("k_spmm", flops * nrhs, bytes, s);
-  k_spmm<<<nrows, 128, 0, s>>>(rows, ents, nrhs);
-  CK_LAUNCH("k_spmm");
-}
 
 // out[t + c ld_out] = in[perm[t] + c ld_in]   (gather: user -> tree order)
 __global__ void k_gather_rows(const long long* __restrict__ perm, long long N,

@@ -4,6 +4,7 @@
 // stream it is launched on, tagged with the kernel name and the algorithmic
 // flops and bytes of that launch.  Collection synchronises once and sums the
 // event intervals per kernel name.
+#include <cstdlib>
 #include <mutex>
 
 #include "internal.cuh"
@@ -46,6 +47,11 @@ static cudaEvent_t get_event() {
 }
 
 bool enabled() { return on; }
+
+Capture*& capture() {
+  thread_local Capture* c = nullptr;
+  return c;
+}
 
 void* begin(const char* name, double flops, double bytes, cudaStream_t s) {
   if (!on) return nullptr;
@@ -110,4 +116,64 @@ int stop(ifmm_kernel_stat* out, int capacity) {
 }
 
 }  // namespace prof
+
+bool graphs_enabled() {
+  static const bool v = [] {
+    const char* e = std::getenv("IFMM_GRAPHS");
+    return !(e && e[0] == '0');
+  }();
+  return v;
+}
+
+void GraphCache::reset() {
+  if (exec) cudaGraphExecDestroy(exec);
+  exec = nullptr;
+  key = -1;
+}
+
+GraphCache::~GraphCache() {
+  reset();
+  if (cs) cudaStreamDestroy(cs);
+}
+
+void run_graph(GraphCache& g, long long key, const char* name, cudaStream_t s,
+               const std::function<void(cudaStream_t)>& body) {
+  if (!graphs_enabled()) {
+    body(s);
+    return;
+  }
+  if (!g.exec || g.key != key) {
+    g.reset();
+    if (!g.cs) CK(cudaStreamCreateWithFlags(&g.cs, cudaStreamNonBlocking));
+    prof::Capture cap;
+    const unsigned long long n0 = launch_counter();
+    CK(cudaStreamBeginCapture(g.cs, cudaStreamCaptureModeThreadLocal));
+    prof::capture() = &cap;
+    cudaGraph_t gr = nullptr;
+    try {
+      body(g.cs);
+    } catch (...) {
+      prof::capture() = nullptr;
+      cudaStreamEndCapture(g.cs, &gr);
+      if (gr) cudaGraphDestroy(gr);
+      cudaGetLastError();
+      launch_counter() = n0;
+      throw;
+    }
+    prof::capture() = nullptr;
+    CK(cudaStreamEndCapture(g.cs, &gr));
+    g.kernels = launch_counter() - n0;
+    launch_counter() = n0;
+    const cudaError_t e = cudaGraphInstantiate(&g.exec, gr, 0);
+    cudaGraphDestroy(gr);
+    CK(e);
+    g.key = key;
+    g.flops = cap.flops;
+    g.bytes = cap.bytes;
+  }
+  Prof p(name, g.flops, g.bytes, s);
+  CK(cudaGraphLaunch(g.exec, s));
+  launch_counter() += g.kernels;
+}
+
 }  // namespace ifmm

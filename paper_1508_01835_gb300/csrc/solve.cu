@@ -14,6 +14,7 @@ namespace ifmm {
 
 static void build_plan(ifmm_factorization* f, int nrhs, cudaStream_t s) {
   SolvePlan& P = f->plan;
+  P.graph.reset();
   P.steps.clear();
   P.mem.release();
   P.task_mem.release();
@@ -68,13 +69,11 @@ static void build_plan(ifmm_factorization* f, int nrhs, cudaStream_t s) {
     if (st.ncopies) P.steps.push_back(std::move(st));
   };
   auto add_spmm = [&](std::vector<SpRow>& rows, std::vector<SpEnt>& ents) {
-    validate_spmm(rows, ents, nrhs);
+    if (rows.empty()) return;
     SolvePlan::Step st;
     st.kind = 2;
-    st.nrows = (int)rows.size();
-    st.rows = upload(P.task_mem, rows, s);
-    st.ents = upload(P.task_mem, ents, s);
-    if (st.nrows) P.steps.push_back(std::move(st));
+    st.sp = plan_spmm(P.task_mem, rows, ents, nrhs, s);
+    P.steps.push_back(std::move(st));
   };
   for (auto& g : groups) {  // forward
     std::vector<CopyTask> cps;
@@ -150,13 +149,15 @@ void factor_solve(ifmm_factorization* f, const double* b, long long ldb, double*
     CK(cudaStreamSynchronize(s));
     return;
   }
-  for (int l = 2; l <= sys->L; l++)
-    CK(cudaMemsetAsync(P.ybar[l], 0, sizeof(double) * std::max(P.nybar[l], 1ll) * nrhs, s));
-  for (const SolvePlan::Step& st : P.steps) {
-    if (st.kind == 0) launch_copy(st.copies, st.ncopies, s);
-    else if (st.kind == 2) launch_spmm(st.rows, st.nrows, st.ents, nrhs, s);
-    else exec_getrs(st.rs, s);
-  }
+  run_graph(P.graph, nrhs, "graph:ifmm_solve", s, [&](cudaStream_t gs) {
+    for (int l = 2; l <= sys->L; l++)
+      CK(cudaMemsetAsync(P.ybar[l], 0, sizeof(double) * std::max(P.nybar[l], 1ll) * nrhs, gs));
+    for (const SolvePlan::Step& st : P.steps) {
+      if (st.kind == 0) launch_copy(st.copies, st.ncopies, gs);
+      else if (st.kind == 2) launch_spmm(st.sp, nrhs, gs);
+      else exec_getrs(st.rs, gs);
+    }
+  });
   launch_scatter_rows(sys->perm, N, P.xt, N, x, ldx, nrhs, s);
 }
 

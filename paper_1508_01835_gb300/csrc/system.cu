@@ -161,7 +161,7 @@ ifmm_system* system_create(ifmm_ctx* ctx, const double* pts, bool host, long lon
   require(opt->eps >= 0.0 && std::isfinite(opt->eps), "eps must be >= 0");
   require(opt->schur >= IFMM_P_FP64 && opt->schur <= IFMM_P_BF16, "unknown Schur precision");
   require(opt->rank_cap >= 0, "rank_cap must be >= 0");
-  require(opt->rsvd_rows >= 0 && opt->rsvd_rows <= SVD_EXACT_MAX_A, "rsvd_rows must be in 0..144");
+  require(opt->rsvd_rows >= 0 && opt->rsvd_rows <= 65536, "rsvd_rows must be in 0..65536");
   require(k->kind >= IFMM_K_INV_R && k->kind <= IFMM_K_PAPER_D, "unknown kernel kind");
   require(!(k->kind == IFMM_K_INV_R && std::isnan(k->diag)), "1/r kernel needs a diagonal");
   require(k->kind == IFMM_K_INV_R || k->param > 0.0, "kernel parameter must be > 0");
@@ -214,6 +214,7 @@ ifmm_system* system_create(ifmm_ctx* ctx, const double* pts, bool host, long lon
 // FMM matvec plan: P2M, M2M per level, M2L + L2L per level, L2P + P2P
 // ---------------------------------------------------------------------------
 static void build_fmm_plan(ifmm_system* sys, int cap, cudaStream_t s) {
+  sys->fmm_graph.reset();
   sys->fmm_plan.phases.clear();
   sys->fmm_plan.mem.reset();
   sys->fmm_ws.release();
@@ -288,7 +289,8 @@ void system_matvec(ifmm_system* sys, int mode, const double* x, long long ldx, d
     build_fmm_plan(sys, std::max(nrhs, 4), s);
   }
   launch_gather_rows(sys->perm, sys->N, x, ldx, sys->fmm_x, sys->N, nrhs, s);
-  sys->fmm_plan.run(nrhs, s);
+  run_graph(sys->fmm_graph, nrhs, "graph:fmm_matvec", s,
+            [&](cudaStream_t gs) { sys->fmm_plan.run(nrhs, gs); });
   launch_scatter_rows(sys->perm, sys->N, sys->fmm_y, sys->N, y, ldy, nrhs, s);
 }
 

@@ -63,18 +63,11 @@ struct ChebOps {
 };
 
 // A launch sequence of block-row products.
-struct SpPhase {
-  SpRow* rows = nullptr;
-  SpEnt* ents = nullptr;
-  int nrows = 0;
-  double flops = 0.0, bytes = 0.0;  // per right-hand side
-};
 struct SpPlan {
-  std::vector<SpPhase> phases;
+  std::vector<SpmmPlan> phases;
   Arena mem;
   void run(int nrhs, cudaStream_t s) const {
-    for (const SpPhase& p : phases)
-      launch_spmm(p.rows, p.nrows, p.ents, nrhs, s, p.flops, p.bytes * nrhs);
+    for (const SpmmPlan& p : phases) launch_spmm(p, nrhs, s);
   }
 };
 struct SpBuild {
@@ -90,20 +83,7 @@ struct SpBuild {
   }
   void flush(SpPlan& plan, cudaStream_t s, int nrhs = 1) {
     if (rows.empty()) return;
-    validate_spmm(rows, ents, nrhs);
-    SpPhase ph;
-    for (const SpRow& R : rows) {
-      ph.bytes += 8.0 * R.m;
-      for (int e = R.e0; e < R.e0 + R.ne; e++) {
-        const SpEnt& E = ents[e];
-        ph.flops += 2.0 * R.m * (double)E.k;
-        ph.bytes += 8.0 * E.k + (E.A ? 8.0 * R.m * (double)E.k : 0.0);
-      }
-    }
-    ph.nrows = (int)rows.size();
-    ph.rows = upload(plan.mem, rows, s);
-    ph.ents = upload(plan.mem, ents, s);
-    plan.phases.push_back(ph);
+    plan.phases.push_back(plan_spmm(plan.mem, rows, ents, nrhs, s));
     rows.clear();
     ents.clear();
   }
@@ -134,6 +114,7 @@ struct ifmm_system {
   // FMM matvec plan and its workspace (grown on demand)
   ifmm::Arena fmm_ws;
   ifmm::SpPlan fmm_plan;
+  ifmm::GraphCache fmm_graph;  // fmm_plan.run as one graph
   int fmm_cap = 0;
   double *fmm_x = nullptr, *fmm_y = nullptr;
   double sigma0 = std::numeric_limits<double>::quiet_NaN();
