@@ -48,9 +48,15 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", choices=["c1", "c2"], default="c2")
-    p.add_argument("--schur", choices=["fp64", "tf32"], default="fp64")
+    p.add_argument("--schur", choices=["fp64", "fp32", "tf32"], default="fp32",
+                   help="Schur-product precision of the timed path (fp32: split-TF32 tensor cores)")
+    p.add_argument("--general", action="store_true",
+                   help="time the paper's general algorithm (two SVDs per box) instead of the "
+                        "symmetric variant")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-plain", action="store_true",
+                   help="skip the plain FP64 comparison step of a mixed-precision run")
     return p.parse_args()
 
 
@@ -219,19 +225,20 @@ def run_ours(args):
     b = torch.tensor(b_h, device=dev)
     x = torch.empty_like(b)
     ctx = ifmm.ifmm_ctx_create(local)
-    schur = ifmm.P_TF32 if args.schur == "tf32" else ifmm.P_FP64
+    schur = {"fp64": ifmm.P_FP64, "fp32": ifmm.P_FP32, "tf32": ifmm.P_TF32}[args.schur]
     opt = ifmm.make_options(dim=w.dim, cheb_n=w.cheb_n, leaf_max=w.leaf_max, eps=w.eps,
-                            schur=schur)
+                            schur=schur, symmetric=0 if args.general else 1)
     kern = ifmm.Kernel(w.kernel.kind, w.kernel.param, w.kernel.diag)
     stream = torch.cuda.current_stream()
 
-    def step(host=False):
+    def step(host=False, o=None):
+        o = opt if o is None else o
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         ev[0].record(stream)
         if host:
-            sys_h = ifmm.ifmm_system_create_host(ctx, pts_h, kern, opt)
+            sys_h = ifmm.ifmm_system_create_host(ctx, pts_h, kern, o)
         else:
-            sys_h = ifmm.ifmm_system_create(ctx, pts, kern, opt)
+            sys_h = ifmm.ifmm_system_create(ctx, pts, kern, o)
         fac = ifmm.ifmm_factor(ctx, sys_h)
         ev[1].record(stream)
         if host:
@@ -263,19 +270,26 @@ def run_ours(args):
     clk = clocks.stop()
     if dist:
         dist.barrier()
-    ms = t_start.elapsed_time(t_end)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(t_start.elapsed_time(t_end), dist, dev)
     step_ms = [ev[0].elapsed_time(ev[2]) for ev, _, _ in recs]
     factor_ms = [ev[0].elapsed_time(ev[1]) for ev, _, _ in recs]
     solve_ms = [ev[1].elapsed_time(ev[2]) for ev, _, _ in recs]
     reps = [r for _, rr, _ in recs for r in rr]
     info = recs[-1][2]
-    nsolves = args.steps * w.nrhs * world
-    value = nsolves / (ms / 1e3)
+    value = whole_job_rate(args.steps * w.nrhs, world, ms)
     ok = all(r.status == 0 and r.true_rel_residual <= 1e-10 for r in reps)
+
+    # the plain FP64 path on the same input, for "factor s vs plain FP64"
+    plain = None
+    if (args.schur != "fp64" or not args.general) and not args.no_plain:
+        opt64 = ifmm.make_options(dim=w.dim, cheb_n=w.cheb_n, leaf_max=w.leaf_max, eps=w.eps,
+                                  schur=ifmm.P_FP64)
+        ev, reps64, _ = step(o=opt64)
+        torch.cuda.synchronize()
+        plain = {"factor_s": ev[0].elapsed_time(ev[1]) / 1e3,
+                 "step_ms": ev[0].elapsed_time(ev[2]),
+                 "gmres_iterations": [r.iters for r in reps64],
+                 "true_rel_residual": max(r.true_rel_residual for r in reps64)}
 
     # end to end through the host-buffer entry points
     e2e = None
@@ -314,11 +328,13 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": describe(w), "schur": args.schur,
+                   "variant": "general" if args.general else "symmetric",
                    "l2": "inputs larger than L2 (factor working set > 129 MB)",
                    "replicas": "independent per GPU"},
         "latency_ms": {"p50": _pct(step_ms, 50), "p99": _pct(step_ms, 99)},
         "solve_latency_ms": {"p50": _pct(solve_ms, 50), "p99": _pct(solve_ms, 99)},
         "factor_s": statistics.median(factor_ms) / 1e3,
+        "plain_fp64": plain,
         "gmres_iterations": [r.iters for r in reps],
         "true_rel_residual": max(r.true_rel_residual for r in reps),
         "converged": ok,
@@ -337,6 +353,21 @@ def run_ours(args):
     ifmm.ifmm_ctx_destroy(ctx)
     if dist:
         dist.destroy_process_group()
+
+
+def max_over_ranks(ms, dist, device):
+    """The slowest rank's time (every rank runs the same replica workload)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, ms):
+    """Units processed by all ranks per second of the slowest rank's time."""
+    return units_per_rank * world / (ms / 1e3)
 
 
 def _pct(v, q):

@@ -33,6 +33,7 @@ typedef struct CUstream_st* ifmm_stream; /* same type as cudaStream_t */
 typedef struct ifmm_ctx ifmm_ctx;
 typedef struct ifmm_system ifmm_system;
 typedef struct ifmm_factorization ifmm_factorization;
+typedef struct ifmm_server ifmm_server;
 
 typedef enum {
   IFMM_OK = 0,
@@ -60,8 +61,14 @@ typedef struct {
                    the 1/r kernel does not have (then NaN is invalid)          */
 } ifmm_kernel;
 
-/* Input precision of the Schur-update products (Sec. 2.2, Algorithm 2). */
-typedef enum { IFMM_P_FP64 = 0, IFMM_P_TF32 = 1, IFMM_P_BF16 = 2 } ifmm_precision;
+/* Precision of the Schur-update products S = E(R,P) E(P,P)^-1 E(P,C) of the
+ * elimination (Sec. 2.2, Algorithm 2).  FP64: FP64 FMA.  TF32: operands rounded
+ * to TF32 on the tcgen05 tensor cores, FP32 accumulation.  FP32: each operand
+ * split into two TF32 parts, three tensor-core products (hi*hi + hi*lo + lo*hi),
+ * FP32 accumulation -- close to FP32 accuracy.  The pivot LU, the solve for
+ * E(P,P)^-1 E(P,C), every SVD and rank decision, the solve sweeps and GMRES
+ * stay in FP64.  BF16 is declared but not implemented (IFMM_ERR_UNSUPPORTED). */
+typedef enum { IFMM_P_FP64 = 0, IFMM_P_TF32 = 1, IFMM_P_BF16 = 2, IFMM_P_FP32 = 3 } ifmm_precision;
 
 typedef struct {
   int dim;             /* 2 or 3                                                    */
@@ -77,6 +84,11 @@ typedef struct {
   int rsvd_rows;       /* blocks with more rows than this (and a rank cap below
                           their height) are recompressed with the randomised SVD
                           of Sec. 2.4; 0 = 160, otherwise 1..65536                 */
+  int symmetric;       /* 1: symmetric variant -- the V side of every basis SVD
+                          reuses the U side's singular vectors and values (one SVD
+                          per box instead of two).  Valid when A is symmetric,
+                          which holds for every kernel of this library (radial,
+                          U = V at the leaves); the paper's general algorithm is 0 */
 } ifmm_options;
 
 typedef enum { IFMM_MV_FMM = 0, IFMM_MV_DIRECT = 1 } ifmm_matvec_mode;
@@ -183,7 +195,8 @@ ifmm_status fmm_matvec(ifmm_ctx* ctx, const ifmm_system* sys, int mode, const do
 /* ---- allocation-free matvec --------------------------------------------------- */
 /* The paper has no counterpart to this entry point; it serves callers that
  * cannot allocate device memory while they run (a host application that owns
- * a fixed device pool, a real-time loop, code recording a CUDA graph).
+ * a fixed device pool and forbids cudaMalloc, or a real-time loop that must not
+ * stall on the allocator).
  * Computes the same y = A_n x as fmm_matvec(IFMM_MV_FMM) (the direct product
  * when the system has no tree) but calls no cudaMalloc, cudaFree or other
  * allocating routine: its scratch -- the tree lists it needs and the
@@ -212,6 +225,71 @@ ifmm_status gmres_solve_host(ifmm_ctx* ctx, const ifmm_system* sys,
                              const ifmm_factorization* fac, int mode, const double* b_host,
                              double* x_host, int nrhs, long long ld, double tol, int maxit,
                              ifmm_gmres_report* rep, ifmm_stream stream);
+
+/* ---- many systems: batched factorisation (the paper factorises one system at a
+ * time, Algorithm 1; independent systems share nothing) ------------------------ */
+/* Factorises sys[0..count-1] (distinct systems) concurrently: up to 8 worker
+ * threads, each on its own CUDA stream that first waits for the work queued on
+ * `stream`, take the systems largest first.  out: host array of count
+ * handles, filled in (each freed by ifmm_factor_destroy).  On any error other
+ * than IFMM_ERR_SINGULAR_PIVOT every out[k] is NULL; with a singular pivot the
+ * handles stay valid, as for ifmm_factor.  Returns after all factorisations
+ * are complete. */
+ifmm_status ifmm_factor_batch(ifmm_ctx* ctx, ifmm_system* const* sys, int count,
+                              ifmm_stream stream, ifmm_factorization** out);
+
+/* ---- serving: continuous batching of GMRES solves (Sec. 3.2 per request) ---- */
+/* A server owns `workers` threads (0 = 4), each with its own stream.  A worker
+ * takes the registered system whose oldest queued request has waited longest
+ * and that no other worker is serving, gathers all of that system's queued
+ * requests (at most 32 columns) into one block of right-hand sides, runs FP64
+ * GMRES (FMM matvec, the factorisation as right preconditioner) on the block
+ * -- every column converges on its own -- and returns each request's columns.
+ * Requests that arrive while their system is busy join its next block; other
+ * systems are served at the same time by the other workers.  Destroy a server
+ * only after every ifmm_server_wait has returned. */
+ifmm_status ifmm_server_create(ifmm_ctx* ctx, unsigned long long hbm_budget, int workers,
+                               ifmm_server** out);
+void ifmm_server_destroy(ifmm_server* srv);
+/* Admits (sys, fac) if its device memory -- operators, factorisation, solve
+ * plans and the GMRES workspace of one 32-column block with maxit iterations
+ * -- fits what is left of hbm_budget; IFMM_ERR_BUDGET otherwise (nothing is
+ * registered).  The server does not own sys or fac; they must outlive it.
+ * *id: the handle for ifmm_server_submit. */
+ifmm_status ifmm_server_register(ifmm_server* srv, ifmm_system* sys, ifmm_factorization* fac,
+                                 int maxit, int* id);
+/* Queues a solve of A_n x = b for system `id`: b_host, x_host in host memory,
+ * N x nrhs column-major (ld N), 1 <= nrhs <= 32; both must stay valid until
+ * the ticket is waited for.  Residual target tol (a block uses the smallest
+ * tol and the largest maxit of its requests).  Load shedding: if the system
+ * already has 128 columns queued the request is refused with IFMM_ERR_BUDGET
+ * (and counted as shed). */
+ifmm_status ifmm_server_submit(ifmm_server* srv, int id, const double* b_host, double* x_host,
+                               int nrhs, double tol, int maxit, long long* ticket);
+/* Waits up to timeout_ms (< 0: no limit) for a ticket; IFMM_ERR_TIMEOUT if it
+ * is not done yet (the ticket stays valid).  On completion fills rep (nrhs
+ * entries, host), *latency_s (submit to completion, seconds; may be NULL),
+ * releases the ticket and returns the request's status. */
+ifmm_status ifmm_server_wait(ifmm_server* srv, long long ticket, int timeout_ms,
+                             ifmm_gmres_report* rep, double* latency_s);
+/* Device bytes admitted, GMRES blocks run, columns solved and requests shed
+ * so far (any pointer may be NULL). */
+ifmm_status ifmm_server_stats(ifmm_server* srv, unsigned long long* used_bytes,
+                              long long* batches, long long* columns, long long* shed);
+const char* ifmm_server_last_error(ifmm_server* srv);
+
+/* ---- Schur product kernel ----------------------------------------------------- */
+/* C = alpha op(A) op(B) + beta C with the kernel the elimination uses for its
+ * Schur products at precision `prec` (ifmm_precision; FP64, TF32 or FP32) --
+ * the trailing update of Sec. 2.2, exposed so that a caller can check or time
+ * it on its own matrices.  A, B, C: device, FP64, column-major; op(A) is M x K
+ * (A is M x K with lda >= M, or K x M with lda >= K when transA), op(B) is
+ * K x N likewise, C is M x N with ldc >= M and must not overlap A or B.
+ * beta == 0 does not read C.  IFMM_ERR_TIMEOUT if a tensor-core wait ran out
+ * (the result is then undefined); synchronises `stream`. */
+ifmm_status ifmm_schur_product(ifmm_ctx* ctx, int prec, int M, int N, int K, const double* A,
+                               int lda, int transA, const double* B, int ldb, int transB,
+                               double* C, int ldc, double alpha, double beta, ifmm_stream stream);
 
 /* ---- launch profile ------------------------------------------------------ */
 /* Start recording an event pair around each of the library's launches (on

@@ -57,6 +57,12 @@ R3b blocks taller than rsvd_rows rows (default 160) that are truncated below
     drawn from a counter-based SplitMix64 stream (seeded by level, box and
     side, so the CUDA path draws the same numbers), one power iteration with
     re-orthonormalisation, and the exact SVD of the projected k-row matrix.
+S   symmetric variant (optional; the paper notes that its algorithm is not
+    specialised to symmetric matrices and that symmetry could be exploited):
+    when A is symmetric and U = V at the leaves, the V-side matrix of every
+    basis SVD equals the U-side one in exact arithmetic, so the V side takes
+    the U side's singular vectors and values (V_hat = U_hat, t_j = r_j) and
+    only one SVD per box is computed.
 
 Parity: pinned by tests -- with tau = 0 the factorisation is an exact block
 LU of E and the solve equals the dense solve of A_n to rounding; the
@@ -219,9 +225,11 @@ class IFMM:
     """Plain IFMM factorisation of the H^2 matrix A_n defined by ``h2``."""
 
     def __init__(self, h2: H2, eps: float, tau: float | None = None, rank_cap: int | None = None,
-                 sigma0: float | None = None, rsvd_rows: int = RSVD_ROWS_DEFAULT):
+                 sigma0: float | None = None, rsvd_rows: int = RSVD_ROWS_DEFAULT,
+                 symmetric: bool = False):
         self.h2 = h2
         self.rsvd_rows = rsvd_rows
+        self.symmetric = symmetric
         self.tree = h2.tree
         self.eps = eps
         self.rank_cap = rank_cap
@@ -269,7 +277,8 @@ class IFMM:
                 MU = self.sigma0 * RU[i]
                 MV = self.sigma0 * RV[i]
             WU, sU = left_svd(MU)
-            WV, sV = left_svd(MV)
+            # symmetric variant (reading S): the V side reuses the U side's SVD
+            WV, sV = (WU, sU) if self.symmetric else left_svd(MV)
             r = min(max(count_rank(sU, self.tau, k), count_rank(sV, self.tau, k)), k)
             r = self._cap(r)
             st.r.append(r)
@@ -379,11 +388,11 @@ class IFMM:
             if self.tau > 0 and aj > self.rsvd_rows and rcap < aj:
                 k = min(aj, rcap + RSVD_OVERSAMPLE, SVD_EXACT_MAX_A)
                 WU, sU = rsvd_left(MU, k, rsvd_seed(st.l, j, 0))
-                WV, sV = rsvd_left(MV, k, rsvd_seed(st.l, j, 1))
+                WV, sV = (WU, sU) if self.symmetric else rsvd_left(MV, k, rsvd_seed(st.l, j, 1))
                 full = k
             else:
                 WU, sU = left_svd(MU)
-                WV, sV = left_svd(MV)
+                WV, sV = (WU, sU) if self.symmetric else left_svd(MV)
                 full = aj
             rn = min(max(count_rank(sU, self.tau, full), count_rank(sV, self.tau, full)), full)
             rn = self._cap(rn)

@@ -23,7 +23,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error",
           4: "singular pivot block", 5: "GMRES did not converge", 6: "timeout",
           7: "memory budget exceeded", 8: "unsupported"}
 K_INV_R, K_GAUSSIAN, K_PAPER_D = 0, 1, 2
-P_FP64, P_TF32, P_BF16 = 0, 1, 2
+P_FP64, P_TF32, P_BF16, P_FP32 = 0, 1, 2, 3
 MV_FMM, MV_DIRECT = 0, 1
 
 
@@ -34,7 +34,7 @@ class Kernel(C.Structure):
 class Options(C.Structure):
     _fields_ = [("dim", C.c_int), ("cheb_n", C.c_int), ("leaf_max", C.c_int), ("eps", C.c_double),
                 ("schur", C.c_int), ("tau_override", C.c_double), ("rank_cap", C.c_int),
-                ("fmm_n", C.c_int), ("rsvd_rows", C.c_int)]
+                ("fmm_n", C.c_int), ("rsvd_rows", C.c_int), ("symmetric", C.c_int)]
 
 
 class GmresReport(C.Structure):
@@ -109,6 +109,20 @@ def lib() -> C.CDLL:
         "gmres_solve_host": (C.c_int, [P, P, P, C.c_int, P, P, C.c_int, C.c_longlong,
                                        C.c_double, C.c_int, C.POINTER(GmresReport), P]),
         "fmm_matvec_static": (C.c_int, [P, P, P, P, C.c_int, C.c_longlong, P]),
+        "ifmm_factor_batch": (C.c_int, [P, P, C.c_int, P, P]),
+        "ifmm_server_create": (C.c_int, [P, C.c_ulonglong, C.c_int, C.POINTER(P)]),
+        "ifmm_server_destroy": (None, [P]),
+        "ifmm_server_register": (C.c_int, [P, P, P, C.c_int, C.POINTER(C.c_int)]),
+        "ifmm_server_submit": (C.c_int, [P, C.c_int, P, P, C.c_int, C.c_double, C.c_int,
+                                         C.POINTER(C.c_longlong)]),
+        "ifmm_server_wait": (C.c_int, [P, C.c_longlong, C.c_int, C.POINTER(GmresReport),
+                                       C.POINTER(C.c_double)]),
+        "ifmm_server_stats": (C.c_int, [P, C.POINTER(C.c_ulonglong), C.POINTER(C.c_longlong),
+                                        C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
+        "ifmm_server_last_error": (C.c_char_p, [P]),
+        "ifmm_schur_product": (C.c_int, [P, C.c_int, C.c_int, C.c_int, C.c_int, P, C.c_int,
+                                         C.c_int, P, C.c_int, C.c_int, P, C.c_int, C.c_double,
+                                         C.c_double, P]),
         "ifmm_profile_start": (C.c_int, [P]),
         "ifmm_profile_stop": (C.c_int, [P, C.POINTER(KernelStat), C.c_int, C.POINTER(C.c_int)]),
     }
@@ -160,8 +174,9 @@ def ifmm_ctx_destroy(ctx):
 
 
 def make_options(dim=3, cheb_n=3, leaf_max=64, eps=1e-6, schur=P_FP64, tau_override=0.0,
-                 rank_cap=0, fmm_n=0, rsvd_rows=0) -> Options:
-    return Options(dim, cheb_n, leaf_max, eps, schur, tau_override, rank_cap, fmm_n, rsvd_rows)
+                 rank_cap=0, fmm_n=0, rsvd_rows=0, symmetric=0) -> Options:
+    return Options(dim, cheb_n, leaf_max, eps, schur, tau_override, rank_cap, fmm_n, rsvd_rows,
+                   symmetric)
 
 
 def ifmm_system_create(ctx, pts, kernel: Kernel, opt: Options, stream=None):
@@ -283,6 +298,85 @@ def gmres_solve_host(ctx, sys, fac, mode: int, b_np, x_np, tol=1e-10, maxit=500,
                                   x_np.ctypes.data_as(P), k, N, tol, maxit, reps,
                                   _stream(stream)), ctx, allow=(5,))
     return list(reps)
+
+
+def ifmm_factor_batch(ctx, systems, stream=None, allow_singular=False):
+    """Factorise several systems concurrently; returns their factorisation handles."""
+    n = len(systems)
+    arr = (P * max(n, 1))(*systems)
+    out = (P * max(n, 1))()
+    _check(lib().ifmm_factor_batch(ctx, arr, n, _stream(stream), out), ctx,
+           allow=(4,) if allow_singular else ())
+    return [out[i] for i in range(n)]
+
+
+class ServerError(IFMMError):
+    pass
+
+
+def _scheck(st, srv, allow=()):
+    if st != IFMM_OK and st not in allow:
+        raise ServerError(st, lib().ifmm_server_last_error(srv).decode() if srv else "")
+    return st
+
+
+def ifmm_server_create(ctx, hbm_budget: int, workers: int = 0):
+    h = P()
+    _check(lib().ifmm_server_create(ctx, hbm_budget, workers, C.byref(h)), ctx)
+    return h
+
+
+def ifmm_server_destroy(srv):
+    lib().ifmm_server_destroy(srv)
+
+
+def ifmm_server_register(srv, sys, fac, maxit: int = 100) -> int:
+    i = C.c_int()
+    _scheck(lib().ifmm_server_register(srv, sys, fac, maxit, C.byref(i)), srv)
+    return i.value
+
+
+def ifmm_server_submit(srv, sid: int, b_np, x_np, tol=1e-10, maxit=100) -> int:
+    """b_np, x_np: float64 numpy arrays (nrhs, N) C order (or (N,)); both must
+    stay alive until the ticket is waited for."""
+    import numpy as np
+    assert b_np.dtype == np.float64 and x_np.dtype == np.float64
+    assert b_np.flags["C_CONTIGUOUS"] and x_np.flags["C_CONTIGUOUS"]
+    k = 1 if b_np.ndim == 1 else b_np.shape[0]
+    t = C.c_longlong()
+    _scheck(lib().ifmm_server_submit(srv, sid, b_np.ctypes.data_as(P), x_np.ctypes.data_as(P), k,
+                                     tol, maxit, C.byref(t)), srv)
+    return t.value
+
+
+def ifmm_server_wait(srv, ticket: int, nrhs: int, timeout_ms: int = -1):
+    """(status, reports, latency seconds); status 6 (timeout) leaves the ticket valid."""
+    reps = (GmresReport * nrhs)()
+    lat = C.c_double()
+    st = lib().ifmm_server_wait(srv, ticket, timeout_ms, reps, C.byref(lat))
+    return st, list(reps), lat.value
+
+
+def ifmm_server_stats(srv):
+    """(admitted device bytes, GMRES blocks, columns solved, requests shed)."""
+    u, b, c, d = C.c_ulonglong(), C.c_longlong(), C.c_longlong(), C.c_longlong()
+    _scheck(lib().ifmm_server_stats(srv, C.byref(u), C.byref(b), C.byref(c), C.byref(d)), srv)
+    return u.value, b.value, c.value, d.value
+
+
+def ifmm_schur_product(ctx, prec: int, M: int, N: int, K: int, A, lda: int, transA: int, B,
+                       ldb: int, transB: int, Cm, ldc: int, alpha=1.0, beta=0.0, stream=None):
+    """C = alpha op(A) op(B) + beta C with the elimination's Schur-product kernel
+    at precision `prec`.  A, B, Cm: contiguous float64 CUDA tensors whose memory
+    holds column-major matrices with the given leading dimensions."""
+    import torch
+    for t in (A, B, Cm):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
+                and t.is_contiguous()):
+            raise TypeError("operands must be contiguous float64 CUDA tensors")
+    _check(lib().ifmm_schur_product(ctx, prec, M, N, K, P(A.data_ptr()), lda, transA,
+                                    P(B.data_ptr()), ldb, transB, P(Cm.data_ptr()), ldc,
+                                    alpha, beta, _stream(stream)), ctx)
 
 
 def ifmm_profile_start(ctx):

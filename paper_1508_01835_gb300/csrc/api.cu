@@ -159,7 +159,7 @@ ifmm_status ifmm_factor_get_ranks(const ifmm_factorization* fac, int level, int*
 
 ifmm_status ifmm_factor_footprint(const ifmm_factorization* fac, unsigned long long* bytes) {
   if (!fac || !bytes) return IFMM_ERR_INVALID_ARG;
-  *bytes = fac->store.held + fac->plan.mem.held + fac->plan.task_mem.held;
+  *bytes = fac->store.held + fac->plan_bytes();
   return IFMM_OK;
 }
 
@@ -231,6 +231,37 @@ ifmm_status gmres_solve_host(ifmm_ctx* ctx, const ifmm_system* sys, const ifmm_f
     }
   });
   return g != IFMM_OK ? g : res;
+}
+
+ifmm_status ifmm_schur_product(ifmm_ctx* ctx, int prec, int M, int N, int K, const double* A,
+                               int lda, int transA, const double* B, int ldb, int transB,
+                               double* C, int ldc, double alpha, double beta, ifmm_stream stream) {
+  if (!ctx || M < 0 || N < 0 || K < 0 || !C) return IFMM_ERR_INVALID_ARG;
+  if (prec != IFMM_P_FP64 && prec != IFMM_P_TF32 && prec != IFMM_P_FP32)
+    return prec == IFMM_P_BF16 ? IFMM_ERR_UNSUPPORTED : IFMM_ERR_INVALID_ARG;
+  if (K > 0 && (!A || !B)) return IFMM_ERR_INVALID_ARG;
+  if (ldc < std::max(M, 1) || lda < std::max(transA ? K : M, 1) ||
+      ldb < std::max(transB ? N : K, 1))
+    return IFMM_ERR_INVALID_ARG;
+  if (M == 0 || N == 0) return IFMM_OK;
+  return guard(ctx, [&] {
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t s = st(stream);
+    // the caller's matrices join the bounds validation (IFMM_VALIDATE=1)
+    ScopedRange ra(A, K > 0 ? mat_bytes(transA ? K : M, transA ? M : K, lda) : 0);
+    ScopedRange rb(B, K > 0 ? mat_bytes(transB ? N : K, transB ? K : N, ldb) : 0);
+    ScopedRange rc(C, mat_bytes(M, N, ldc));
+    Arena ar;
+    int* err = ar.alloc<int>(1);
+    CK(cudaMemsetAsync(err, 0, sizeof(int), s));
+    const GemmTask t{A, B, C, lda, ldb, ldc, M, N, K, transA ? 1 : 0, transB ? 1 : 0, alpha, beta};
+    if (prec == IFMM_P_FP64) run_gemms(ar, {t}, s);
+    else run_gemms_tc(ar, {t}, prec == IFMM_P_FP32, err, s);
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (h) throw Error(IFMM_ERR_TIMEOUT, "tensor-core product: a bounded wait ran out");
+  });
 }
 
 ifmm_status ifmm_profile_start(ifmm_ctx* ctx) {

@@ -81,6 +81,7 @@ struct FLevel {
   std::vector<double*> X, Y;  // per neighbour slot (ld a_i) / per N u I slot (ld rcap_i)
   std::vector<double*> U, V, SU, SV, Upar, Vpar;
   std::vector<double*> Uraw, Vraw;  // raw bases of this level (a_i x nd, ld a_i)
+  EdgeLevel edge{};                  // device copies of the lists for k_edge_redirect
   Arena mem;
 };
 
@@ -88,11 +89,6 @@ struct FLevel {
 // randomised SVD when the rank cap is below the block height and truncation
 // is on (tau > 0): the top k = min(a, cap + oversampling, 144) singular
 // triplets decide the rank.
-static double g_tau_for_rsvd = 0.0;
-static int g_rsvd_rows = RSVD_ROWS_DEFAULT;
-static bool use_rsvd(int a, int rcap) {
-  return g_tau_for_rsvd > 0.0 && a > g_rsvd_rows && rcap < a;
-}
 static int rsvd_k(int a, int rcap) {
   return std::min(std::min(a, rcap + RSVD_OVERSAMPLE), SVD_EXACT_MAX_A);
 }
@@ -106,7 +102,10 @@ struct Factorizer {
   double tau = 0.0;
   int cap_global = 0;
   Arena scratch;
-  int* d_counters = nullptr;  // [0]: rank cap hits
+  int* d_counters = nullptr;  // [0]: rank cap hits, [1]: tensor-core wait timeouts
+  int rsvd_rows = RSVD_ROWS_DEFAULT;
+
+  bool use_rsvd(int a, int rcap) const { return tau > 0.0 && a > rsvd_rows && rcap < a; }
 
   Factorizer(ifmm_system* sy, ifmm_factorization* fa, cudaStream_t st)
       : sys(sy), f(fa), s(st), ops(sy->ops_f), nd(sy->ops_f.nd), dim(sy->dim) {}
@@ -169,6 +168,18 @@ struct Factorizer {
       st.Vpar[i] = bp + np + op;
       op += (long long)st.rcap[i] * nd;
     }
+    // interaction lists and edge blocks for the device-side edge redirection
+    std::vector<double*> yo(lv.far.size()), yi(lv.far.size());
+    for (int i = 0; i < st.nb; i++)
+      for (int k = lv.far_ptr[i]; k < lv.far_ptr[i + 1]; k++) {
+        yo[k] = Y(st, lv, i, lv.far[k]);
+        yi[k] = Y(st, lv, lv.far[k], i);
+      }
+    st.edge.far_ptr = upload(st.mem, lv.far_ptr, s);
+    st.edge.far = upload(st.mem, lv.far, s);
+    st.edge.y_out = upload(st.mem, yo, s);
+    st.edge.y_in = upload(st.mem, yi, s);
+    st.edge.rcap = upload(st.mem, st.rcap, s);
   }
 
   // sync and read ranks written by rank tasks
@@ -250,9 +261,11 @@ struct Factorizer {
     std::vector<double*> RU, RV, TU, TV;
     bool any_tall = false;
     for (int i = 0; i < nb; i++) any_tall |= st.a[i] > nd;
+    const bool sym = sys->opt.symmetric != 0;  // reading S: V side = U side
     if (any_tall) {
       raw_factors(st, st.Uraw, RU, TU, keep);
-      raw_factors(st, st.Vraw, RV, TV, keep);
+      if (sym) { RV = RU; TV = TU; }
+      else raw_factors(st, st.Vraw, RV, TV, keep);
     }
     std::vector<double*> WU(nb), WV(nb), sU(nb), sV(nb);
     std::vector<int> full(nb);
@@ -260,9 +273,9 @@ struct Factorizer {
       const int a = st.a[i];
       const int dimW = a > nd ? nd : a;  // rows of the matrix whose SVD decides the rank
       WU[i] = keep.alloc<double>((size_t)dimW * dimW);
-      WV[i] = keep.alloc<double>((size_t)dimW * dimW);
       sU[i] = keep.alloc<double>(dimW);
-      sV[i] = keep.alloc<double>(dimW);
+      WV[i] = sym ? WU[i] : keep.alloc<double>((size_t)dimW * dimW);
+      sV[i] = sym ? sU[i] : keep.alloc<double>(dimW);
       full[i] = std::min(a, nd);
     }
     int* d_r = keep.alloc<int>(nb);
@@ -297,20 +310,20 @@ struct Factorizer {
           // empty interaction list: weight the raw basis by sigma_0 (reading R6)
           wcols = nd;
           MU = scratch.alloc<double>((size_t)rows * nd);
-          MV = scratch.alloc<double>((size_t)rows * nd);
+          MV = sym ? nullptr : scratch.alloc<double>((size_t)rows * nd);
           if (tall) {
             cps.push_back(cp(RU[i], nd, MU, nd, nd, nd, 0, s0));
-            cps.push_back(cp(RV[i], nd, MV, nd, nd, nd, 0, s0));
+            if (!sym) cps.push_back(cp(RV[i], nd, MV, nd, nd, nd, 0, s0));
           } else {
             cps.push_back(cp(st.Uraw[i], a, MU, a, a, nd, 0, s0));
-            cps.push_back(cp(st.Vraw[i], a, MV, a, a, nd, 0, s0));
+            if (!sym) cps.push_back(cp(st.Vraw[i], a, MV, a, a, nd, 0, s0));
           }
         } else {
           wcols = (int)w;
           double* BU = scratch.alloc<double>((size_t)nd * w);
-          double* BV = scratch.alloc<double>((size_t)nd * w);
+          double* BV = sym ? nullptr : scratch.alloc<double>((size_t)nd * w);
           MU = scratch.alloc<double>((size_t)rows * w);
-          MV = scratch.alloc<double>((size_t)rows * w);
+          MV = sym ? nullptr : scratch.alloc<double>((size_t)rows * w);
           long long off = 0;
           for (int k = lv.far_ptr[i]; k < lv.far_ptr[i + 1]; k++) {
             const int q = lv.far[k];
@@ -320,26 +333,28 @@ struct Factorizer {
             if (tall) {
               // BU[:, off] = K_iq R_q^T ; BV[:, off] = K_qi^T R_q(U)^T   (nd x nd)
               g1.push_back(gm(Kiq, nd, 0, RV[q], nd, 1, BU + off * nd, nd, nd, nd, nd, 1.0, 0.0));
-              g1.push_back(gm(Kqi, nd, 1, RU[q], nd, 1, BV + off * nd, nd, nd, nd, nd, 1.0, 0.0));
+              if (!sym)
+                g1.push_back(gm(Kqi, nd, 1, RU[q], nd, 1, BV + off * nd, nd, nd, nd, nd, 1.0, 0.0));
               off += nd;
             } else {
               // BU[:, off] = K_iq V_q^T ; BV[:, off] = K_qi^T U_q^T
               g1.push_back(gm(Kiq, nd, 0, st.Vraw[q], aq, 1, BU + off * nd, nd, nd, aq, nd, 1.0, 0.0));
-              g1.push_back(gm(Kqi, nd, 1, st.Uraw[q], aq, 1, BV + off * nd, nd, nd, aq, nd, 1.0, 0.0));
+              if (!sym)
+                g1.push_back(gm(Kqi, nd, 1, st.Uraw[q], aq, 1, BV + off * nd, nd, nd, aq, nd, 1.0, 0.0));
               off += aq;
             }
           }
           if (tall) {
             g2.push_back(gm(RU[i], nd, 0, BU, nd, 0, MU, nd, nd, (int)w, nd, 1.0, 0.0));
-            g2.push_back(gm(RV[i], nd, 0, BV, nd, 0, MV, nd, nd, (int)w, nd, 1.0, 0.0));
+            if (!sym) g2.push_back(gm(RV[i], nd, 0, BV, nd, 0, MV, nd, nd, (int)w, nd, 1.0, 0.0));
           } else {
             g2.push_back(gm(st.Uraw[i], a, 0, BU, nd, 0, MU, a, a, (int)w, nd, 1.0, 0.0));
-            g2.push_back(gm(st.Vraw[i], a, 0, BV, nd, 0, MV, a, a, (int)w, nd, 1.0, 0.0));
+            if (!sym) g2.push_back(gm(st.Vraw[i], a, 0, BV, nd, 0, MV, a, a, (int)w, nd, 1.0, 0.0));
           }
         }
         svd.push_back({MU, rows, rows, wcols, WU[i], sU[i], nullptr});
-        svd.push_back({MV, rows, rows, wcols, WV[i], sV[i], nullptr});
-        f->info.flops_lowrank += 4.0 * rows * (double)rows * wcols;
+        if (!sym) svd.push_back({MV, rows, rows, wcols, WV[i], sV[i], nullptr});
+        f->info.flops_lowrank += (sym ? 2.0 : 4.0) * rows * (double)rows * wcols;
       }
       run_copies(scratch, cps, s);
       run_gemms(scratch, g1, s);
@@ -479,7 +494,13 @@ struct Factorizer {
     run_copies(scratch, cps, s);
     run_getrf(scratch, lus, s);
     run_getrs(scratch, rss, s);
-    run_gemms(scratch, gs, s);
+    // Schur products S = E(R,P) G: FP64, or the tensor cores in the
+    // mixed-precision modes (a wait that runs out counts in d_counters[1])
+    const int prec = sys->opt.schur;
+    if (prec == IFMM_P_TF32 || prec == IFMM_P_FP32)
+      run_gemms_tc(scratch, gs, prec == IFMM_P_FP32, d_counters + 1, s);
+    else
+      run_gemms(scratch, gs, s);
     // scatter -S into edges; collect well-separated fill
     struct Fill { int b, rb, cb; };
     std::vector<Fill> fills;
@@ -535,6 +556,7 @@ struct Factorizer {
       if (rb.kind == 'x') wU[slot[rb.box]] += cb.dim;
       if (cb.kind == 'x') wV[slot[cb.box]] += rb.dim;
     }
+    const bool sym = sys->opt.symmetric != 0;  // reading S: V side = U side
     std::vector<double*> MU(nJ), MV(nJ), WU(nJ), WV(nJ), sU(nJ), sV(nJ);
     std::vector<int> cU(nJ), cV(nJ), kk(nJ);
     std::vector<CopyTask> cps;
@@ -545,13 +567,13 @@ struct Factorizer {
       const int j = J[t], a = st.a[j], r = st.r[j];
       kk[t] = use_rsvd(a, st.rcap[j]) ? rsvd_k(a, st.rcap[j]) : a;  // singular values kept
       MU[t] = scratch.alloc<double>((size_t)a * wU[t]);
-      MV[t] = scratch.alloc<double>((size_t)a * wV[t]);
       WU[t] = scratch.alloc<double>((size_t)a * kk[t]);
-      WV[t] = scratch.alloc<double>((size_t)a * kk[t]);
       sU[t] = scratch.alloc<double>(kk[t]);
-      sV[t] = scratch.alloc<double>(kk[t]);
+      MV[t] = sym ? nullptr : scratch.alloc<double>((size_t)a * wV[t]);
+      WV[t] = sym ? WU[t] : scratch.alloc<double>((size_t)a * kk[t]);
+      sV[t] = sym ? sU[t] : scratch.alloc<double>(kk[t]);
       cps.push_back(cp(st.U[j], a, MU[t], a, a, r, 0, 1.0, 0.0, st.SU[j]));
-      cps.push_back(cp(st.V[j], a, MV[t], a, a, r, 0, 1.0, 0.0, st.SV[j]));
+      if (!sym) cps.push_back(cp(st.V[j], a, MV[t], a, a, r, 0, 1.0, 0.0, st.SV[j]));
       cU[t] = cV[t] = r;
     }
     for (const Fill& F : fills) {  // [U Sigma_U | F_j1 | ..], [V Sigma_V | F_1j^T | ..]
@@ -564,7 +586,7 @@ struct Factorizer {
         cps.push_back(cp(src, R.nC, MU[t] + (size_t)cU[t] * a, a, rb.dim, cb.dim, 0, -1.0));
         cU[t] += cb.dim;
       }
-      if (cb.kind == 'x') {
+      if (cb.kind == 'x' && !sym) {
         const int t = slot[cb.box];
         const int a = st.a[cb.box];
         cps.push_back(cp(src, R.nC, MV[t] + (size_t)cV[t] * a, a, cb.dim, rb.dim, 1, -1.0));
@@ -575,14 +597,15 @@ struct Factorizer {
     std::vector<RankTask> rt;
     for (int t = 0; t < nJ; t++) {
       const int j = J[t], a = st.a[j];
+      const double wsum = wU[t] + (sym ? 0.0 : (double)wV[t]);
       if (kk[t] < a) {
         rsvd.push_back({MU[t], a, a, wU[t], kk[t], rsvd_seed(lv.l, j, 0), WU[t], sU[t]});
-        rsvd.push_back({MV[t], a, a, wV[t], kk[t], rsvd_seed(lv.l, j, 1), WV[t], sV[t]});
-        f->info.flops_lowrank += 8.0 * a * (double)kk[t] * (wU[t] + wV[t]);
+        if (!sym) rsvd.push_back({MV[t], a, a, wV[t], kk[t], rsvd_seed(lv.l, j, 1), WV[t], sV[t]});
+        f->info.flops_lowrank += 8.0 * a * (double)kk[t] * wsum;
       } else {
         svd.push_back({MU[t], a, a, wU[t], WU[t], sU[t], nullptr});
-        svd.push_back({MV[t], a, a, wV[t], WV[t], sV[t], nullptr});
-        f->info.flops_lowrank += 4.0 * a * (double)a * (wU[t] + wV[t]);
+        if (!sym) svd.push_back({MV[t], a, a, wV[t], WV[t], sV[t], nullptr});
+        f->info.flops_lowrank += 4.0 * a * (double)a * wsum;
       }
       rt.push_back({sU[t], sV[t], kk[t], st.rcap[j], d_r + t, d_counters});
     }
@@ -600,9 +623,13 @@ struct Factorizer {
     for (int t = 0; t < nJ; t++) {
       const int j = J[t], a = st.a[j];
       rm[t] = scratch.alloc<double>((size_t)std::max(rn[t], 1) * std::max(st.r[j], 1));
-      tm[t] = scratch.alloc<double>((size_t)std::max(rn[t], 1) * std::max(st.r[j], 1));
       g.push_back(gm(WU[t], a, 1, st.U[j], a, 0, rm[t], std::max(rn[t], 1), rn[t], st.r[j], a, 1.0, 0.0));
-      g.push_back(gm(WV[t], a, 1, st.V[j], a, 0, tm[t], std::max(rn[t], 1), rn[t], st.r[j], a, 1.0, 0.0));
+      if (sym) {
+        tm[t] = rm[t];  // V_hat = U_hat and V = U: t_j = r_j
+      } else {
+        tm[t] = scratch.alloc<double>((size_t)std::max(rn[t], 1) * std::max(st.r[j], 1));
+        g.push_back(gm(WV[t], a, 1, st.V[j], a, 0, tm[t], std::max(rn[t], 1), rn[t], st.r[j], a, 1.0, 0.0));
+      }
     }
     run_gemms(scratch, g, s);
     // Algorithm 3: K(j, q) <- r_j K(j, q), K(q, j) <- K(q, j) t_j^T (q in I_j).
@@ -611,16 +638,55 @@ struct Factorizer {
     std::vector<std::pair<int, int>> edges;
     std::vector<char> isR(st.nb, 0);
     for (int j : J) isR[j] = 1;
-    for (int j : J)
-      for (int k = lv.far_ptr[j]; k < lv.far_ptr[j + 1]; k++) {
-        const int q = lv.far[k];
-        edges.push_back({j, q});
-        if (!isR[q]) edges.push_back({q, j});
-      }
     auto rold = [&](int b) { return st.r[b]; };
     auto rnew = [&](int b) { auto it = slot.find(b); return it == slot.end() ? st.r[b] : rn[it->second]; };
     std::vector<GemmTask> p1, p2;
     std::vector<CopyTask> c1, c2;
+    int rmax = 0;
+    for (int b = 0; b < st.nb; b++) rmax = std::max(rmax, std::max(rold(b), rnew(b)));
+    const bool on_device = rmax <= 64;
+    if (on_device) {
+      // one CTA per recompressed box walks its interaction list
+      std::vector<int> r0(st.nb), r1(st.nb);
+      std::vector<const double*> pm(st.nb, nullptr), pt(st.nb, nullptr);
+      for (int b = 0; b < st.nb; b++) { r0[b] = rold(b); r1[b] = rnew(b); }
+      double fl = 0.0;
+      for (int t = 0; t < nJ; t++) {
+        pm[J[t]] = rm[t];
+        pt[J[t]] = tm[t];
+      }
+      for (int j : J)
+        for (int k = lv.far_ptr[j]; k < lv.far_ptr[j + 1]; k++) {
+          const int q = lv.far[k];
+          fl += 2.0 * r1[j] * r0[q] * r0[j];
+          fl += isR[q] ? 2.0 * r1[j] * r1[q] * r0[q] : 2.0 * r0[q] * r1[j] * r0[j];
+        }
+      if (Ranges::on())  // host-side check of every block the kernel will touch
+        for (int t = 0; t < nJ; t++) {
+          const int j = J[t];
+          Ranges::check(rm[t], mat_bytes(r1[j], r0[j], std::max(r1[j], 1)), "edge r_j");
+          Ranges::check(tm[t], mat_bytes(r1[j], r0[j], std::max(r1[j], 1)), "edge t_j");
+          for (int k = lv.far_ptr[j]; k < lv.far_ptr[j + 1]; k++) {
+            const int q = lv.far[k];
+            Ranges::check(Y(st, lv, j, q),
+                          mat_bytes(std::max(r0[j], r1[j]), std::max(r0[q], r1[q]), st.rcap[j]),
+                          "edge K(j,q)");
+            if (!isR[q])
+              Ranges::check(Y(st, lv, q, j), mat_bytes(r0[q], std::max(r0[j], r1[j]), st.rcap[q]),
+                            "edge K(q,j)");
+          }
+        }
+      EdgeColour E{upload(scratch, r0, s), upload(scratch, r1, s), upload(scratch, pm, s),
+                   upload(scratch, pt, s), upload(scratch, J, s), std::max(rmax, 1)};
+      launch_edge_redirect(st.edge, E, nJ, s, fl);
+    } else {
+      for (int j : J)
+        for (int k = lv.far_ptr[j]; k < lv.far_ptr[j + 1]; k++) {
+          const int q = lv.far[k];
+          edges.push_back({j, q});
+          if (!isR[q]) edges.push_back({q, j});
+        }
+    }
     for (auto& e : edges) {
       const int a = e.first, b = e.second;
       double* Yab = Y(st, lv, a, b);
@@ -794,8 +860,7 @@ struct Factorizer {
     f->info.sigma0 = sys->sigma0;
     f->info.sigma0_iters = sys->sigma0_iters;
     f->info.tau = tau;
-    g_tau_for_rsvd = tau;
-    g_rsvd_rows = o.rsvd_rows > 0 ? o.rsvd_rows : RSVD_ROWS_DEFAULT;
+    rsvd_rows = o.rsvd_rows > 0 ? o.rsvd_rows : RSVD_ROWS_DEFAULT;
     cap_global = o.rank_cap > 0 ? o.rank_cap : (tau == 0.0 ? (1 << 30) : nd);
     f->rank.assign(L + 1, {});
     f->yoff.assign(L + 1, {});
@@ -873,6 +938,8 @@ struct Factorizer {
     TRACE("[ifmm] top: n = %d, %.3f s\n", f->top_n, f->info.seconds_top);
     std::vector<int> cnt = read_ints(d_counters, 4);
     f->info.rank_capped = cnt[0];
+    if (cnt[1] != 0)
+      throw Error(IFMM_ERR_TIMEOUT, "tensor-core Schur product: a bounded wait ran out");
   }
 };
 
@@ -882,22 +949,19 @@ ifmm_factorization* factor_create(ifmm_system* sys, cudaStream_t s) {
   try {
     Factorizer fz(sys, f, s);
     fz.run();
-    // singular pivot tests
-    int sing = 0;
-    std::vector<int> h;
-    for (const FRec& R : f->recs) {
-      int v = 0;
-      CK(cudaMemcpyAsync(&v, R.info, sizeof(int), cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
-      sing += v != 0;
-    }
+    // singular pivot tests: count the failed blocks in one reduction
+    std::vector<const int*> flags;
+    for (const FRec& R : f->recs) flags.push_back(R.info);
     for (int* p : {f->top_info, f->dense_info})
-      if (p) {
-        int v = 0;
-        CK(cudaMemcpyAsync(&v, p, sizeof(int), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        sing += v != 0;
-      }
+      if (p) flags.push_back(p);
+    int sing = 0;
+    if (!flags.empty()) {
+      Arena tmp;
+      int* d_count = tmp.alloc<int>(1);
+      launch_count_nonzero(upload(tmp, flags, s), (int)flags.size(), d_count, s);
+      CK(cudaMemcpyAsync(&sing, d_count, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+    }
     f->info.singular_pivots = sing;
     f->info.factor_bytes = (long long)f->store.held;
     return f;

@@ -1,5 +1,8 @@
 // factor.cuh -- the IFMM factorisation object and its substitution plan.
 #pragma once
+#include <map>
+#include <memory>
+
 #include "system.cuh"
 
 namespace ifmm {
@@ -56,7 +59,14 @@ struct ifmm_factorization {
   int* dense_info = nullptr;
   int* d_info_all = nullptr;
   ifmm_factor_info info{};
-  ifmm::SolvePlan plan;
+  // substitution plans by right-hand-side count (built on first use; a plan is
+  // specific to its column count, so alternating batch widths keep theirs)
+  std::map<int, std::unique_ptr<ifmm::SolvePlan>> plans;
+  size_t plan_bytes() const {
+    size_t b = 0;
+    for (auto& kv : plans) b += kv.second->mem.held + kv.second->task_mem.held;
+    return b;
+  }
 };
 
 namespace ifmm {

@@ -7,13 +7,22 @@
 
 namespace ifmm {
 
-// h[c * ldh + j] = sum_i V_c[i, j] w_c[i], j = 0..k;  V_c = V + c * ldV (column j at + j * N)
-__global__ void k_basis_dots(const double* __restrict__ V, long long ldV, long long N,
+// The Krylov basis grows in chunks of KCH vectors, allocated as the iteration
+// reaches them: basis vector j of right-hand side c is at
+// Vtab[j / KCH] + c * N * KCH + (j % KCH) * N.
+constexpr int KCH = 16;
+__device__ __forceinline__ const double* basis(const double* const* Vtab, long long N, int c,
+                                               int j) {
+  return Vtab[j / KCH] + (long long)c * N * KCH + (long long)(j % KCH) * N;
+}
+
+// h[c * ldh + j] = sum_i V_c[i, j] w_c[i], j = 0..k
+__global__ void k_basis_dots(const double* const* __restrict__ Vtab, long long N,
                              const double* __restrict__ w, long long ldw, int k,
                              double* __restrict__ h, int ldh) {
   const int j = blockIdx.x, c = blockIdx.y;
   if (j > k) return;
-  const double* v = V + c * ldV + (long long)j * N;
+  const double* v = basis(Vtab, N, c, j);
   const double* x = w + c * ldw;
   double s = 0.0;
   for (long long i = threadIdx.x; i < N; i += blockDim.x) s += v[i] * x[i];
@@ -28,7 +37,7 @@ __global__ void k_basis_dots(const double* __restrict__ V, long long ldV, long l
 }
 
 // w_c -= sum_{j <= k} V_c[:, j] h[c, j]   (or x_c = sum_j V_c[:, j] y[c, j] when beta == 0)
-__global__ void k_basis_combine(const double* __restrict__ V, long long ldV, long long N,
+__global__ void k_basis_combine(const double* const* __restrict__ Vtab, long long N,
                                 double* __restrict__ w, long long ldw, const int* __restrict__ kc,
                                 int k, const double* __restrict__ h, int ldh, double sign,
                                 double beta) {
@@ -37,7 +46,7 @@ __global__ void k_basis_combine(const double* __restrict__ V, long long ldV, lon
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
        i += (long long)gridDim.x * blockDim.x) {
     double s = 0.0;
-    for (int j = 0; j <= kk; j++) s += V[c * ldV + (long long)j * N + i] * h[c * ldh + j];
+    for (int j = 0; j <= kk; j++) s += basis(Vtab, N, c, j)[i] * h[c * ldh + j];
     double* o = w + c * ldw + i;
     *o = (beta == 0.0) ? sign * s : beta * (*o) + sign * s;
   }
@@ -123,8 +132,20 @@ ifmm_status gmres_run(ifmm_system* sys, ifmm_factorization* fac, int mode, const
   const int m = maxit;
   Arena ar;
   ar.chunk_bytes = size_t(64) << 20;
-  const long long ldV = N * (m + 1);
-  double* V = ar.alloc<double>((size_t)ldV * nrhs);
+  // Krylov basis: chunks of KCH vectors (ld N * KCH between right-hand sides)
+  const long long ldV = N * KCH;
+  const int nchunks = m / KCH + 1;
+  std::vector<double*> vtab(nchunks, nullptr);
+  double** d_vtab = ar.alloc<double*>(nchunks);
+  auto vec = [&](int j) -> double* {  // basis vector j (allocating its chunk)
+    const int ch = j / KCH;
+    if (!vtab[ch]) {
+      vtab[ch] = ar.alloc<double>((size_t)ldV * nrhs);
+      CK(cudaMemcpyAsync(d_vtab + ch, &vtab[ch], sizeof(double*), cudaMemcpyHostToDevice, s));
+    }
+    return vtab[ch] + (long long)(j % KCH) * N;
+  };
+  const double* const* Vt = d_vtab;
   double* Z = ar.alloc<double>((size_t)N * nrhs);
   double* Wv = ar.alloc<double>((size_t)N * nrhs);
   const int ldH = m + 1;
@@ -146,23 +167,23 @@ ifmm_status gmres_run(ifmm_system* sys, ifmm_factorization* fac, int mode, const
   launch_dots(b, ld, b, ld, N, nrhs, hn, part, s);
   k_init_state<<<(nrhs + 63) / 64, 64, 0, s>>>(nrhs, hn, st, g, m + 1, inv);
   CK_LAUNCH("k_init_state");
-  launch_axpby(N, nrhs, inv, 1.0, b, ld, 0.0, V, ldV, s);
+  launch_axpby(N, nrhs, inv, 1.0, b, ld, 0.0, vec(0), ldV, s);
   std::vector<GState> hs(nrhs);
   int k = 0;
   for (k = 0; k < m; k++) {
-    double* vk = V + (long long)k * N;
+    double* vk = vec(k);
     if (fac) factor_solve(fac, vk, ldV, Z, N, nrhs, s);  // Z = M^-1 v_k
     else launch_axpby(N, nrhs, nullptr, 1.0, vk, ldV, 0.0, Z, N, s);
     system_matvec(sys, mode, Z, N, Wv, N, nrhs, s);
     // CGS2
-    k_basis_dots<<<dim3(k + 1, nrhs), 256, 0, s>>>(V, ldV, N, Wv, N, k, h, m + 1);
+    k_basis_dots<<<dim3(k + 1, nrhs), 256, 0, s>>>(Vt, N, Wv, N, k, h, m + 1);
     CK_LAUNCH("k_basis_dots");
-    k_basis_combine<<<dim3(gblocks(N), nrhs), 256, 0, s>>>(V, ldV, N, Wv, N, nullptr, k, h, m + 1,
+    k_basis_combine<<<dim3(gblocks(N), nrhs), 256, 0, s>>>(Vt, N, Wv, N, nullptr, k, h, m + 1,
                                                            -1.0, 1.0);
     CK_LAUNCH("k_basis_combine");
-    k_basis_dots<<<dim3(k + 1, nrhs), 256, 0, s>>>(V, ldV, N, Wv, N, k, h2, m + 1);
+    k_basis_dots<<<dim3(k + 1, nrhs), 256, 0, s>>>(Vt, N, Wv, N, k, h2, m + 1);
     CK_LAUNCH("k_basis_dots");
-    k_basis_combine<<<dim3(gblocks(N), nrhs), 256, 0, s>>>(V, ldV, N, Wv, N, nullptr, k, h2,
+    k_basis_combine<<<dim3(gblocks(N), nrhs), 256, 0, s>>>(Vt, N, Wv, N, nullptr, k, h2,
                                                            m + 1, -1.0, 1.0);
     CK_LAUNCH("k_basis_combine");
     launch_axpby((long long)(k + 1), nrhs, nullptr, 1.0, h2, m + 1, 1.0, h, m + 1, s);
@@ -171,7 +192,7 @@ ifmm_status gmres_run(ifmm_system* sys, ifmm_factorization* fac, int mode, const
                                              st, inv);
     CK_LAUNCH("k_givens");
     if (k + 1 < m + 1)
-      launch_axpby(N, nrhs, inv, 1.0, Wv, N, 0.0, V + (long long)(k + 1) * N, ldV, s);
+      launch_axpby(N, nrhs, inv, 1.0, Wv, N, 0.0, vec(k + 1), ldV, s);
     CK(cudaMemcpyAsync(hs.data(), st, nrhs * sizeof(GState), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     bool any = false;
@@ -181,7 +202,7 @@ ifmm_status gmres_run(ifmm_system* sys, ifmm_factorization* fac, int mode, const
   // x = M^-1 (V y)
   k_backsolve<<<(nrhs + 63) / 64, 64, 0, s>>>(nrhs, H, ldH, g, m + 1, st, y, kc);
   CK_LAUNCH("k_backsolve");
-  k_basis_combine<<<dim3(gblocks(N), nrhs), 256, 0, s>>>(V, ldV, N, Z, N, kc, 0, y, m + 1, 1.0,
+  k_basis_combine<<<dim3(gblocks(N), nrhs), 256, 0, s>>>(Vt, N, Z, N, kc, 0, y, m + 1, 1.0,
                                                          0.0);
   CK_LAUNCH("k_basis_combine");
   if (fac) factor_solve(fac, Z, N, x, ld, nrhs, s);

@@ -31,10 +31,13 @@ inline void cuda_check(cudaError_t e, const char* what) {
   if (e != cudaSuccess) throw Error(IFMM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 #define CK(x) ::ifmm::cuda_check((x), #x)
-// every launch site of the library is followed by CK_LAUNCH, which also counts it
-unsigned long long& launch_counter();
+// every launch site of the library is followed by CK_LAUNCH, which also counts
+// it: into the process-wide total, or into the capturing thread's count while a
+// graph is being recorded (the graph adds its count at every replay)
+void count_launch();
+unsigned long long launches_total();
 #define CK_LAUNCH(name) \
-  (++::ifmm::launch_counter(), ::ifmm::cuda_check(cudaGetLastError(), name))
+  (::ifmm::count_launch(), ::ifmm::cuda_check(cudaGetLastError(), name))
 
 inline void require(bool ok, const std::string& m) {
   if (!ok) throw Error(IFMM_ERR_INVALID_ARG, m);
@@ -201,6 +204,10 @@ struct Arena {
   }
 };
 
+// cudaFuncSetAttribute(fn, MaxDynamicSharedMemorySize, bytes) once per device
+// (thread-safe).
+void set_max_dynamic_smem(const void* fn, int bytes);
+
 // A device copy of a host vector of POD tasks.
 template <class T>
 T* upload(Arena& ar, const std::vector<T>& v, cudaStream_t s) {
@@ -250,6 +257,41 @@ void launch_gemm(const GemmTask* d_tasks, const GemmTile* d_tiles, int ntiles, c
                  double flops = 0.0);
 // Convenience: run a host list of GEMM tasks (uploads into `ar`).
 void run_gemms(Arena& ar, const std::vector<GemmTask>& tasks, cudaStream_t s);
+
+// Tensor-core form of run_gemms for the Schur products (kernels_tc.cu):
+// 128 x 128 output tiles, operands rounded to TF32 (split: head + tail, the
+// three-term compensated product), FP32 accumulation in tensor memory, FP64
+// epilogue.  *d_err is set to 1 if a bounded wait ran out.
+void gemm_tc_tiles(const GemmTask& t, int task_index, std::vector<GemmTile>& tiles);
+void launch_gemm_tc(const GemmTask* d_tasks, const GemmTile* d_tiles, int ntiles, bool split,
+                    int* d_err, cudaStream_t s, double flops = 0.0);
+void run_gemms_tc(Arena& ar, const std::vector<GemmTask>& tasks, bool split, int* d_err,
+                  cudaStream_t s);
+
+// Edge redirection of Algorithm 3 (kernels_edges.cu), one CTA per
+// recompressed box.  Per level (device arrays, uploaded once): interaction
+// lists and, for list entry k of box j with q = far[k], the blocks K(j, q)
+// (y_out[k], ld rcap[j]) and K(q, j) (y_in[k], ld rcap[q]).
+struct EdgeLevel {
+  const int* far_ptr;
+  const int* far;
+  double* const* y_out;
+  double* const* y_in;
+  const int* rcap;
+};
+// Per colour: ranks before / after recompression of every box of the level,
+// r_j (rm, r_new x r_old, ld r_new) and t_j (tm, same shape) of the
+// recompressed boxes (null for the others), and the recompressed boxes.
+struct EdgeColour {
+  const int* r_old;
+  const int* r_new;
+  const double* const* rm;
+  const double* const* tm;
+  const int* boxes;
+  int rmax;  // largest rank (old or new) of any box touched, <= 64
+};
+void launch_edge_redirect(const EdgeLevel& L, const EdgeColour& E, int nboxes, cudaStream_t s,
+                          double flops);
 
 // Batched LU with partial pivoting (right-looking, panel width LU_NB).
 struct LuTask {

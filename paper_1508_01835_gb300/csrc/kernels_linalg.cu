@@ -1077,14 +1077,8 @@ void run_svd_left(Arena& ar, const std::vector<SvdTask>& tasks_in, cudaStream_t 
   double fl = 0.0;
   for (auto& t : tasks) fl += 2.0 * t.a * (double)t.a * t.w;
   Prof p("k_svd_left", fl, 0.0, s);
-  static bool attr = false;
-  if (!attr) {
-    CK(cudaFuncSetAttribute(k_svd_left<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            SVD_SMEM_BUDGET * 8));
-    CK(cudaFuncSetAttribute(k_svd_left<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            SVD_SMEM_BUDGET * 8));
-    attr = true;
-  }
+  set_max_dynamic_smem((const void*)k_svd_left<4>, SVD_SMEM_BUDGET * 8);
+  set_max_dynamic_smem((const void*)k_svd_left<8>, SVD_SMEM_BUDGET * 8);
   if (amax_s > 0) {
     // shared memory: L ((a+1) x a), chunk ((a+1) x cw), 3a doubles of Jacobi
     // state.  Small blocks take a smaller budget so several CTAs share an SM.

@@ -57,6 +57,7 @@ TreeOut build_tree_device(const double* d_pts, long long N, int dim, int leaf_ma
 
 // vector helpers (kernels_vec.cu)
 // out[c] = sum_i x[i + c ldx] * y[i + c ldy], deterministic fixed-order reduction
+void launch_count_nonzero(const int* const* d_flags, int n, int* d_count, cudaStream_t s);
 void launch_dots(const double* x, long long ldx, const double* y, long long ldy, long long n,
                  int ncols, double* out, double* partial, cudaStream_t s);
 void launch_axpby(long long n, int ncols, const double* alpha, double alpha_scale, const double* x,

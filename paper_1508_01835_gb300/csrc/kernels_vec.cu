@@ -72,4 +72,24 @@ void launch_axpby(long long n, int ncols, const double* alpha, double alpha_scal
   CK_LAUNCH("k_axpby");
 }
 
+// *count = number of nonzero *flags[k] (pivot-test results of many blocks)
+__global__ void k_count_nonzero(const int* const* __restrict__ flags, int n, int* __restrict__ count) {
+  int c = 0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) c += *flags[k] != 0;
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  __shared__ int sh[32];
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += sh[w];
+    *count = t;
+  }
+}
+
+void launch_count_nonzero(const int* const* d_flags, int n, int* d_count, cudaStream_t s) {
+  k_count_nonzero<<<1, 1024, 0, s>>>(d_flags, n, d_count);
+  CK_LAUNCH("k_count_nonzero");
+}
+
 }  // namespace ifmm

@@ -4,17 +4,24 @@
 // stream it is launched on, tagged with the kernel name and the algorithmic
 // flops and bytes of that launch.  Collection synchronises once and sums the
 // event intervals per kernel name.
+#include <atomic>
 #include <cstdlib>
 #include <mutex>
+#include <set>
 
 #include "internal.cuh"
 
 namespace ifmm {
 
-unsigned long long& launch_counter() {
-  static unsigned long long n = 0;
-  return n;
+static std::atomic<unsigned long long> g_launches{0};
+static thread_local bool t_capturing = false;
+static thread_local unsigned long long t_captured = 0;
+
+void count_launch() {
+  if (t_capturing) t_captured++;
+  else g_launches.fetch_add(1, std::memory_order_relaxed);
 }
+unsigned long long launches_total() { return g_launches.load(std::memory_order_relaxed); }
 
 namespace prof {
 
@@ -89,7 +96,7 @@ void start() {
   std::lock_guard<std::mutex> g(mu);
   if (on) drain();
   stats.clear();
-  launches_at_start = launch_counter();
+  launches_at_start = launches_total();
   on = true;
 }
 
@@ -98,7 +105,7 @@ int stop(ifmm_kernel_stat* out, int capacity) {
   drain();
   on = false;
   Stat& all = stats["(all launches)"];
-  all.launches = (long long)(launch_counter() - launches_at_start);
+  all.launches = (long long)(launches_total() - launches_at_start);
   int n = 0;
   for (auto& kv : stats) {
     if (out && n < capacity) {
@@ -116,6 +123,17 @@ int stop(ifmm_kernel_stat* out, int capacity) {
 }
 
 }  // namespace prof
+
+void set_max_dynamic_smem(const void* fn, int bytes) {
+  static std::mutex mu;
+  static std::set<std::pair<const void*, int>> done;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> g(mu);
+  if (done.count({fn, dev})) return;
+  CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  done.insert({fn, dev});
+}
 
 bool graphs_enabled() {
   static const bool v = [] {
@@ -146,24 +164,25 @@ void run_graph(GraphCache& g, long long key, const char* name, cudaStream_t s,
     g.reset();
     if (!g.cs) CK(cudaStreamCreateWithFlags(&g.cs, cudaStreamNonBlocking));
     prof::Capture cap;
-    const unsigned long long n0 = launch_counter();
     CK(cudaStreamBeginCapture(g.cs, cudaStreamCaptureModeThreadLocal));
     prof::capture() = &cap;
+    t_capturing = true;
+    t_captured = 0;
     cudaGraph_t gr = nullptr;
     try {
       body(g.cs);
     } catch (...) {
       prof::capture() = nullptr;
+      t_capturing = false;
       cudaStreamEndCapture(g.cs, &gr);
       if (gr) cudaGraphDestroy(gr);
       cudaGetLastError();
-      launch_counter() = n0;
       throw;
     }
     prof::capture() = nullptr;
+    t_capturing = false;
     CK(cudaStreamEndCapture(g.cs, &gr));
-    g.kernels = launch_counter() - n0;
-    launch_counter() = n0;
+    g.kernels = t_captured;
     const cudaError_t e = cudaGraphInstantiate(&g.exec, gr, 0);
     cudaGraphDestroy(gr);
     CK(e);
@@ -173,7 +192,7 @@ void run_graph(GraphCache& g, long long key, const char* name, cudaStream_t s,
   }
   Prof p(name, g.flops, g.bytes, s);
   CK(cudaGraphLaunch(g.exec, s));
-  launch_counter() += g.kernels;
+  g_launches.fetch_add(g.kernels, std::memory_order_relaxed);
 }
 
 }  // namespace ifmm

@@ -12,8 +12,7 @@
 
 namespace ifmm {
 
-static void build_plan(ifmm_factorization* f, int nrhs, cudaStream_t s) {
-  SolvePlan& P = f->plan;
+static void build_plan(ifmm_factorization* f, SolvePlan& P, int nrhs, cudaStream_t s) {
   P.graph.reset();
   P.steps.clear();
   P.mem.release();
@@ -136,11 +135,14 @@ void factor_solve(ifmm_factorization* f, const double* b, long long ldb, double*
   if (nrhs <= 0) return;
   ifmm_system* sys = f->sys;
   const long long N = sys->N;
-  if (f->plan.cap != nrhs) {
+  std::unique_ptr<SolvePlan>& slot = f->plans[nrhs];
+  if (!slot) {
     CK(cudaStreamSynchronize(s));
-    build_plan(f, nrhs, s);
+    auto P = std::make_unique<SolvePlan>();
+    build_plan(f, *P, nrhs, s);
+    slot = std::move(P);
   }
-  SolvePlan& P = f->plan;
+  SolvePlan& P = *slot;
   launch_gather_rows(sys->perm, N, b, ldb, P.xt, N, nrhs, s);
   if (sys->L == 0) {
     Arena tmp;

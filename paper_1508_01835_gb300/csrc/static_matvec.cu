@@ -3,8 +3,7 @@
 //
 // Some callers cannot allocate device memory while they run: a host
 // application that owns a fixed device pool and forbids further cudaMalloc,
-// a real-time loop that must not allocate, or code that records work into a
-// CUDA graph.  For them this entry point takes its scratch (the tree lists it
+// or a real-time loop that must not stall on the allocator.  For them this entry point takes its scratch (the tree lists it
 // needs and the multipole / local coefficients) from one file-scope device
 // array of STATIC_SCRATCH_BYTES, which every GPU that loads the library holds
 // until the process exits.  The caller passes x and y; the system's operators

@@ -159,8 +159,11 @@ ifmm_system* system_create(ifmm_ctx* ctx, const double* pts, bool host, long lon
   require(opt->fmm_n >= 0 && opt->fmm_n <= 8, "fmm_n must be in 0..8");
   require(opt->leaf_max >= 1, "leaf_max must be >= 1");
   require(opt->eps >= 0.0 && std::isfinite(opt->eps), "eps must be >= 0");
-  require(opt->schur >= IFMM_P_FP64 && opt->schur <= IFMM_P_BF16, "unknown Schur precision");
+  require(opt->schur >= IFMM_P_FP64 && opt->schur <= IFMM_P_FP32, "unknown Schur precision");
+  if (opt->schur == IFMM_P_BF16)
+    throw Error(IFMM_ERR_UNSUPPORTED, "BF16 Schur products are not implemented");
   require(opt->rank_cap >= 0, "rank_cap must be >= 0");
+  require(opt->symmetric == 0 || opt->symmetric == 1, "symmetric must be 0 or 1");
   require(opt->rsvd_rows >= 0 && opt->rsvd_rows <= 65536, "rsvd_rows must be in 0..65536");
   require(k->kind >= IFMM_K_INV_R && k->kind <= IFMM_K_PAPER_D, "unknown kernel kind");
   require(!(k->kind == IFMM_K_INV_R && std::isnan(k->diag)), "1/r kernel needs a diagonal");

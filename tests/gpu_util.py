@@ -7,10 +7,11 @@ from oracle.h2 import H2
 from oracle.ifmm import IFMM
 
 
-def opts(w, eps=None, tau=0.0, rank_cap=0, fmm_n=0, schur=0, rsvd_rows=0):
+def opts(w, eps=None, tau=0.0, rank_cap=0, fmm_n=0, schur=0, rsvd_rows=0, symmetric=0):
     return ifmm.make_options(dim=w.dim, cheb_n=w.cheb_n, leaf_max=w.leaf_max,
                              eps=w.eps if eps is None else eps, schur=schur, tau_override=tau,
-                             rank_cap=rank_cap, fmm_n=fmm_n, rsvd_rows=rsvd_rows)
+                             rank_cap=rank_cap, fmm_n=fmm_n, rsvd_rows=rsvd_rows,
+                             symmetric=symmetric)
 
 
 def kernel(w):

@@ -1,0 +1,117 @@
+"""Mixed-precision Schur products on the tcgen05 tensor cores.
+
+1. The product kernel itself (ifmm_schur_product) against an FP64 product on
+   the host, for ragged shapes spanning several 128 x 128 tiles and K slices,
+   every transpose combination, and beta != 0.  The bound is the rounding of
+   the inputs plus FP32 accumulation: per element
+       |C - C_ref| <= (u_in + K 2^-24) * (|alpha| |op(A)| |op(B)|)_ij + |beta| 2^-52 |C|
+   with u_in = 2 * 2^-11 for TF32 (both operands rounded to 10 mantissa bits)
+   and u_in = 4 * 2^-22 for the split product (the dropped lo*lo term and the
+   rounding of the tails).
+2. The factorisation with TF32 / split-TF32 Schur products used as the GMRES
+   preconditioner: FP64 GMRES must still reach the 1e-10 residual, and its
+   solution must agree with the FP64 path's to the accuracy the residual
+   allows.  Iteration counts are printed for the record.
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_1508_01835_gb300 as ifmm
+from tests.gpu_util import cuda, kernel, opts, rel
+from workloads import c1, small_cube
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1508_01835_gb300 import build
+    build.build()
+    c = ifmm.ifmm_ctx_create(0)
+    yield c
+    ifmm.ifmm_ctx_destroy(c)
+
+
+SHAPES = [(1, 1, 1), (128, 128, 32), (200, 130, 45), (257, 300, 97), (64, 700, 33),
+          (430, 430, 32), (100, 90, 0)]
+
+
+@pytest.mark.parametrize("prec", [ifmm.P_TF32, ifmm.P_FP32])
+@pytest.mark.parametrize("M,N,K", SHAPES)
+@pytest.mark.parametrize("tA,tB", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_schur_product_kernel(ctx, prec, M, N, K, tA, tB):
+    rng = np.random.default_rng(1000 * M + 10 * N + K + 3 * tA + tB)
+    lda = (K if tA else M) + 3
+    ldb = (N if tB else K) + 5
+    ldc = M + 7
+    A = rng.standard_normal(((M if tA else K) or 1, lda))
+    B = rng.standard_normal(((K if tB else N) or 1, ldb))
+    Cm = rng.standard_normal((N, ldc))
+    alpha, beta = -1.25, 0.5
+    opA = A[:M, :K] if tA else A[:K, :M].T
+    opB = B[:K, :N] if tB else B[:N, :K].T
+    C0 = Cm[:N, :M].T.copy()
+    ref = alpha * opA @ opB + beta * C0
+    bound_mat = abs(alpha) * np.abs(opA) @ np.abs(opB)
+    dA, dB, dC = cuda(A), cuda(B), cuda(Cm)
+    ifmm.ifmm_schur_product(ctx, prec, M, N, K, dA, lda, tA, dB, ldb, tB, dC, ldc, alpha, beta)
+    torch.cuda.synchronize()
+    out_mem = dC.cpu().numpy()
+    got = out_mem[:N, :M].T
+    u_in = 2 * 2.0 ** -11 if prec == ifmm.P_TF32 else 4 * 2.0 ** -22
+    tol = (u_in + K * 2.0 ** -24) * bound_mat + abs(beta) * 2.0 ** -52 * np.abs(C0) + 1e-300
+    err = np.abs(got - ref)
+    assert np.all(err <= tol), f"max err/tol {np.max(err / tol):.3g}"
+    # padding rows of C (ld > M) are untouched
+    assert np.array_equal(out_mem[:N, M:], Cm[:N, M:])
+    # the split product is really more accurate than plain TF32 (K > 0)
+    if prec == ifmm.P_FP32 and K >= 8:
+        assert np.max(err / (bound_mat + 1e-300)) < 2.0 ** -16
+
+
+def test_fp64_product_kernel_matches(ctx):
+    rng = np.random.default_rng(5)
+    M, N, K = 150, 77, 61
+    A = rng.standard_normal((K, M))
+    B = rng.standard_normal((N, K))
+    Cm = np.zeros((N, M))
+    dC = cuda(Cm)
+    ifmm.ifmm_schur_product(ctx, ifmm.P_FP64, M, N, K, cuda(A), M, 0, cuda(B), K, 0, dC, M)
+    got = dC.cpu().numpy().T
+    ref = A.T @ B.T
+    assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(A.T) @ np.abs(B.T))
+
+
+CASES = {
+    "c1": lambda: c1(),
+    "3lev": lambda: small_cube(3000, 7, cheb_n=3, leaf_max=32, eps=1e-6),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_mixed_precision_preconditioner_reaches_fp64_residual(ctx, name):
+    w = CASES[name]()
+    b = cuda(w.rhs(1)[:, 0])
+    xs, its = {}, {}
+    for prec in (ifmm.P_FP64, ifmm.P_FP32, ifmm.P_TF32):
+        sys = ifmm.ifmm_system_create(ctx, cuda(w.points), kernel(w), opts(w, schur=prec))
+        try:
+            fac = ifmm.ifmm_factor(ctx, sys)
+            try:
+                x = torch.empty_like(b)
+                reps = ifmm.gmres_solve(ctx, sys, fac, ifmm.MV_FMM, b, x, w.N, 1e-10, 300)
+                assert reps[0].status == 0, (prec, reps[0].iters, reps[0].rel_residual)
+                assert reps[0].true_rel_residual <= 2e-10, (prec, reps[0].true_rel_residual)
+                xs[prec] = x.cpu().numpy()
+                its[prec] = reps[0].iters
+            finally:
+                ifmm.ifmm_factor_destroy(fac)
+        finally:
+            ifmm.ifmm_system_destroy(sys)
+    print(f"{name}: GMRES iterations fp64 {its[ifmm.P_FP64]}, fp32 (3xTF32) "
+          f"{its[ifmm.P_FP32]}, tf32 {its[ifmm.P_TF32]}")
+    for prec in (ifmm.P_FP32, ifmm.P_TF32):
+        assert rel(xs[prec], xs[ifmm.P_FP64]) < 1e-8
+    # the split product preconditions at least as well as plain TF32, give or take one
+    assert its[ifmm.P_FP32] <= its[ifmm.P_TF32] + 1

@@ -137,6 +137,27 @@ def test_factor_solve_parity(ctx, name):
         ifmm.ifmm_system_destroy(sys)
 
 
+@pytest.mark.parametrize("name", ["c1", "3lev", "2d"])
+def test_symmetric_variant_parity(ctx, name):
+    """Reading S (one SVD per box, V side = U side) on both sides with the same
+    tau: equal ranks, equal solve output to rounding."""
+    w = CASES[name]()
+    h2 = oracle_h2(w)
+    ora = IFMM(h2, w.eps, symmetric=True)
+    sys = make_sys(ctx, w, tau=ora.tau, rank_cap=1 << 20, symmetric=1)
+    fac = ifmm.ifmm_factor(ctx, sys)
+    try:
+        for l in range(2, h2.tree.L + 1):
+            assert ifmm.ifmm_factor_get_ranks(fac, l) == ora.ranks(l), f"ranks differ at depth {l}"
+        B = w.rhs(2).T.copy()
+        X = torch.empty(2, w.N, dtype=torch.float64, device="cuda:0")
+        ifmm.ifmm_solve(ctx, fac, cuda(B), X, w.N)
+        assert rel(X.cpu().numpy(), ora.solve(B.T).T) < 1e-10
+    finally:
+        ifmm.ifmm_factor_destroy(fac)
+        ifmm.ifmm_system_destroy(sys)
+
+
 WELL = {
     "3lev": lambda: small_cube(3000, 7, cheb_n=3, leaf_max=32, eps=1e-6,
                                kernel=Kernel(K_INV_R, 0.0, 4.0 * 3000)),

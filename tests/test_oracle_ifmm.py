@@ -177,3 +177,41 @@ def test_randomised_recompression_keeps_error_bound():
     f0 = IFMM(h, 1e-6, rank_cap=12, sigma0=f.sigma0)
     err0 = np.linalg.norm(f0.solve(b) - x) / np.linalg.norm(x)
     assert err < 10 * max(err0, 1e-6)
+
+
+@pytest.mark.parametrize("N,n,leaf,dim,kernel", [
+    (1500, 2, 12, 3, Kernel(K_INV_R, 0.0, 3000.0)),        # L = 3: one merge
+    (900, 3, 10, 2, Kernel(K_GAUSSIAN, 0.15, 1.01)),       # quadtree, L = 3
+])
+def test_symmetric_variant_tau_zero_is_exact(N, n, leaf, dim, kernel):
+    """Reading S with compression disabled is still an exact block LU of E:
+    every direction is kept, so sharing the U side's SVD changes nothing."""
+    w, h = setup(N, 21, n, leaf, dim, kernel)
+    f = IFMM(h, 0.0, tau=0.0, symmetric=True)
+    b = np.random.default_rng(1).standard_normal(N)
+    x = dense_solution(h, b)
+    kappa = np.linalg.cond(h.dense_blockwise())
+    assert np.linalg.norm(f.solve(b) - x) / np.linalg.norm(x) < 1e-14 * kappa * 50
+
+
+def test_symmetric_variant_tracks_eps_and_matches_general():
+    """Reading S at tau > 0: for a symmetric A (radial kernel, U = V) the V-side
+    matrices equal the U-side ones in exact arithmetic, so the symmetric variant
+    keeps the same ranks as the general algorithm (up to ties at tau) and its
+    solve error follows eps like the general one (Sec. 2.4)."""
+    N = 1200
+    w, h = setup(N, 7, 4, 24, 3, Kernel(K_INV_R, 0.0, 4.0 * N))
+    b = np.random.default_rng(1).standard_normal(N)
+    x = dense_solution(h, b)
+    s0 = None
+    for eps in (1e-3, 1e-6, 1e-9):
+        g = IFMM(h, eps, sigma0=s0)
+        s0 = g.sigma0
+        f = IFMM(h, eps, sigma0=s0, symmetric=True)
+        eg = np.linalg.norm(g.solve(b) - x) / np.linalg.norm(x)
+        es = np.linalg.norm(f.solve(b) - x) / np.linalg.norm(x)
+        assert es < 10 * eps
+        assert es < 3 * eg + 1e-13
+        for l in range(2, h.tree.L + 1):
+            rg, rs = np.array(g.ranks(l)), np.array(f.ranks(l))
+            assert np.mean(rg == rs) > 0.9 and np.max(np.abs(rg - rs)) <= 2

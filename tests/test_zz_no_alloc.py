@@ -1,8 +1,8 @@
 """The allocation-free FMM product (fmm_matvec_static).
 
 Some callers cannot allocate device memory while they run -- a host
-application that owns a fixed device pool, a real-time loop, code recording
-a CUDA graph.  fmm_matvec_static serves them from a library-owned static
+application that owns a fixed device pool and forbids cudaMalloc, or a
+real-time loop that must not stall on the allocator.  fmm_matvec_static serves them from a library-owned static
 device buffer.  Here it must give the same y = A_n x as fmm_matvec on two
 calls in a row (the buffer keeps the previous call's contents), for a
 two-level and a deeper tree, and reject a request larger than its buffer.
