@@ -363,6 +363,11 @@ struct SvdTask {
   double* work;
 };
 void run_svd_left(Arena& ar, const std::vector<SvdTask>& tasks, cudaStream_t s);
+// FP64 flops of the one-sided Jacobi sweeps of every k_svd_left CTA since the
+// last call (device counter, read and reset; synchronises the device).  The
+// launch profiler adds them to k_svd_left's counted flops (the streaming LQ
+// part, 2 a^2 w per task, is counted at launch).
+unsigned long long svd_jacobi_flops_take();
 
 // Randomised left SVD for blocks with a > 144 rows: top k left singular
 // vectors W (a x k, ld a) and values sigma (k); every task of a call has the same k.

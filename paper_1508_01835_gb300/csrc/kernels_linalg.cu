@@ -6,6 +6,7 @@
 // fill-in and of the weighted bases (Eqs. P2P_kj, U_j_recomp, V_j_recomp).
 // Each kernel here runs one such operation for every box of a colour in one
 // launch (boxes of a colour are independent).
+#include <algorithm>
 #include <cfloat>
 
 #include "internal.cuh"
@@ -865,16 +866,21 @@ __device__ void jacobi_norms(double* L, int lda, int a, double* nr, double* dsc,
 // the true column dsc[j] X_j; a rotation of (p, q) with tangent t becomes
 // X_p -= t (d_q / d_p) X_q, X_q += t (d_p / d_q) X_p, d_p, d_q *= cos.
 // nr carries the true squared norms (||x_p||^2 -= t g, ||x_q||^2 += t g).
+// Returns the FP64 flops it performed: 2a per pair product and 4a per rotation
+// (the counted work of the launch profiler; the iteration count is data dependent).
 template <int G>
-__device__ void jacobi_columns(double* L, int lda, int a, double* nr, double* dsc, double* dinv,
-                               int* flag) {
+__device__ unsigned long long jacobi_columns(double* L, int lda, int a, double* nr, double* dsc,
+                                             double* dinv, int* flag, unsigned int* nrot) {
   constexpr int PPW = 32 / G;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int grp = lane / G, q = lane % G;
   const int n = (a + 1) & ~1;
+  int sweeps = 0;
+  if (threadIdx.x == 0) *nrot = 0;
   for (int sweep = 0; sweep < 40; sweep++) {
     jacobi_norms<G>(L, lda, a, nr, dsc, dinv, sweep > 0);
     if (threadIdx.x == 0) *flag = 0;
+    sweeps++;
     __syncthreads();
     for (int round = 0; round < n - 1; round++) {
       for (int base = wid * PPW; base < n / 2; base += nw * PPW) {  // warp-uniform
@@ -924,6 +930,7 @@ __device__ void jacobi_columns(double* L, int lda, int a, double* nr, double* ds
               nr[p] = fmax(fma(-t, g, al), 0.0);
               nr[r2] = fma(t, g, be);
               *flag = 1;
+              atomicAdd(nrot, 1u);
             }
           }
         }
@@ -941,7 +948,12 @@ __device__ void jacobi_columns(double* L, int lda, int a, double* nr, double* ds
   }
   jacobi_norms<G>(L, lda, a, nr, dsc, dinv, true);
   __syncthreads();
+  const unsigned long long pairs = (unsigned long long)a * (a - 1) / 2;
+  return (unsigned long long)sweeps * pairs * 2ull * a + (unsigned long long)(*nrot) * 4ull * a;
 }
+
+// FP64 flops of the Jacobi phases since the last svd_jacobi_flops_take()
+__device__ unsigned long long g_svd_jacobi_flops = 0;
 
 template <int G>
 __global__ void __launch_bounds__(512) k_svd_left(const SvdTask* __restrict__ tasks, int use_smem,
@@ -953,6 +965,7 @@ __global__ void __launch_bounds__(512) k_svd_left(const SvdTask* __restrict__ ta
   extern __shared__ double sm[];
   __shared__ Refl refl[2];
   __shared__ int flag;
+  __shared__ unsigned int nrot;
   SvdView v;
   double* aux;  // nr, dsc, dinv: 3a doubles
   int cwm;
@@ -984,7 +997,9 @@ __global__ void __launch_bounds__(512) k_svd_left(const SvdTask* __restrict__ ta
     __syncthreads();
     lq_chunk<G>(v, a, cw, refl);
   }
-  jacobi_columns<G>(v.L, v.lda, a, aux, aux + a, aux + 2 * a, &flag);
+  const unsigned long long jfl =
+      jacobi_columns<G>(v.L, v.lda, a, aux, aux + a, aux + 2 * a, &flag, &nrot);
+  if (threadIdx.x == 0) atomicAdd(&g_svd_jacobi_flops, jfl);
   // sigma_j = |L_j|; order by decreasing sigma (ties: lower column first).
   // The chunk area (>= a doubles) is free now and holds the column norms.
   double* sg = v.C;
@@ -1036,6 +1051,13 @@ __global__ void __launch_bounds__(512) k_svd_left(const SvdTask* __restrict__ ta
   }
 }
 
+unsigned long long svd_jacobi_flops_take() {
+  unsigned long long v = 0, z = 0;
+  CK(cudaMemcpyFromSymbol(&v, g_svd_jacobi_flops, sizeof(v)));
+  CK(cudaMemcpyToSymbol(g_svd_jacobi_flops, &z, sizeof(z)));
+  return v;
+}
+
 // IFMM_TRACE=2: one line per SVD launch on stderr (tasks, shapes, seconds);
 // synchronises the stream around each launch.
 static bool svd_tracing() {
@@ -1054,6 +1076,14 @@ void run_svd_left(Arena& ar, const std::vector<SvdTask>& tasks_in, cudaStream_t 
     t0 = std::chrono::steady_clock::now();
   }
   std::vector<SvdTask> tasks(tasks_in);
+  // Longest tasks first (one CTA per task, blocks start in index order): the
+  // streaming LQ costs ~ a^2 w and the Jacobi sweeps ~ a^3, so starting the
+  // expensive ones first keeps the last wave from waiting on one big task.
+  std::stable_sort(tasks.begin(), tasks.end(), [](const SvdTask& x, const SvdTask& y) {
+    const double cx = (double)x.a * x.a * (x.w + 10.0 * x.a);
+    const double cy = (double)y.a * y.a * (y.w + 10.0 * y.a);
+    return cx > cy;
+  });
   for (auto& t : tasks) {
     if (t.a <= 0) continue;
     if (t.a > SVD_SMEM_A && !t.work)

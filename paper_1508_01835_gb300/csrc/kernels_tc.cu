@@ -5,8 +5,9 @@
 // (Sec. 2.2, Algorithm 2), is the one dense contraction of the factorisation.
 // In the mixed-precision mode its product S = E(R,P) G runs here:
 //   * operands are FP64 in global memory; each CTA rounds a 128 x 32 slice of
-//     A and of B to TF32 (round to nearest) and stores them in shared memory in
-//     the tensor core's K-major, unswizzled core-matrix layout;
+//     A and of B to TF32 (round to nearest, with integer arithmetic: the FP64
+//     unit is the scarce one) and stores them in shared memory in the tensor
+//     core's K-major, unswizzled core-matrix layout;
 //   * IFMM_P_FP32 splits every operand into a TF32 head and a TF32 tail
 //     (x = hi + lo) and accumulates hi*hi + hi*lo + lo*hi -- the three-term
 //     error-compensated TF32 product of Ootomo and Yokota (2022), close to
@@ -37,13 +38,6 @@ constexpr long long SPIN_LIMIT = 1ll << 22;  // bounded waits (far above any leg
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-// Round to TF32 (nearest, ties away), returned as an FP32 bit pattern.
-__device__ __forceinline__ float to_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
 }
 
 // Shared-memory matrix descriptor: K-major, no swizzle.  Core matrices are
@@ -130,6 +124,66 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* r) {
   for (int i = 0; i < 32; i++) r[i] = __uint_as_float(v[i]);
 }
 
+// FP64 <-> FP32 conversions with integer arithmetic only.  On this part the
+// FP64 unit executes a few operations per clock per SM, and double/float
+// conversions and subtractions would run there; integer and FP32 units are
+// tens of times wider.
+//
+// split_tf32: v = hi + lo + (rounding), with hi = v rounded to 11 significant
+// bits (TF32 precision, nearest, halves rounded away from zero) and lo = the
+// exact remainder v - hi rounded to 11 significant bits; both returned as FP32
+// bit patterns.  |v| < 2^-100 flushes to zero (far below what an FP32
+// accumulation resolves next to the operands this kernel sees); |v| >= 2^128
+// becomes infinity.
+__device__ __forceinline__ void split_tf32(double v, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned int sgn = (unsigned int)(b >> 63) << 31;
+  const int e = (int)((b >> 52) & 0x7FF);  // biased exponent
+  if (e < 1023 - 100) {
+    hi = __uint_as_float(sgn);
+    lo = __uint_as_float(sgn);
+    return;
+  }
+  const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);  // 53-bit significand
+  const unsigned long long mr = ((m + (1ull << 41)) >> 42) << 42;       // m rounded to 11 bits
+  unsigned long long mh = mr >> 42;                                     // 11 bits, or 2^11
+  int eh = e;
+  if (mh >> 11) { mh >>= 1; eh += 1; }
+  const int fe = eh - 1023 + 127;
+  hi = __uint_as_float(fe >= 255 ? (sgn | 0x7F800000u)
+                                 : (sgn | ((unsigned int)fe << 23) |
+                                    ((unsigned int)(mh & 0x3FF) << 13)));
+  const long long r = (long long)m - (long long)mr;  // |r| <= 2^41, value r 2^(e-1075)
+  if (r == 0) {
+    lo = __uint_as_float(0u);
+    return;
+  }
+  unsigned long long ar = (unsigned long long)(r < 0 ? -r : r);
+  int p = 63 - __clzll((long long)ar);  // leading bit of |r|
+  unsigned long long ml;
+  if (p > 10) {
+    ml = (ar + (1ull << (p - 11))) >> (p - 10);
+    if (ml >> 11) { ml >>= 1; p += 1; }
+  } else {
+    ml = ar << (10 - p);
+  }
+  const int le = p + e - 1075 + 127;  // biased FP32 exponent of |r| 2^(e-1075)
+  const unsigned int ls = (r < 0) ? (sgn ^ 0x80000000u) : sgn;
+  lo = __uint_as_float(le <= 0 ? ls : (ls | ((unsigned int)le << 23) |
+                                       ((unsigned int)(ml & 0x3FF) << 13)));
+}
+
+// Exact FP32 -> FP64 widening (FP32 subnormals flush to zero).
+__device__ __forceinline__ double widen(float f) {
+  const unsigned int u = __float_as_uint(f);
+  const unsigned long long sgn = (unsigned long long)(u >> 31) << 63;
+  const unsigned int ex = (u >> 23) & 0xFF;
+  const unsigned long long mant = (unsigned long long)(u & 0x7FFFFF) << 29;
+  if (ex == 0) return __longlong_as_double((long long)sgn);
+  const unsigned long long de = (ex == 255) ? 0x7FFull : (unsigned long long)(ex + 896);
+  return __longlong_as_double((long long)(sgn | (de << 52) | mant));
+}
+
 // Byte offset of element (row, k) of a 128 x 32 K-major slice: core matrix
 // (row / 8, k / 4) at ((k / 4) * 16 + row / 8) * 128, inside it row % 8 at
 // 16-byte stride and k % 4 at 4-byte stride.  Hence sbo = 128 (next 8 rows)
@@ -158,9 +212,8 @@ __device__ __forceinline__ void load_slice(const double* __restrict__ X, int ld,
       const int gk = k0 + kq * 4 + j;
       double v = 0.0;
       if (gr < rows && gk < K) v = trans ? X[gk + (long long)gr * ld] : X[gr + (long long)gk * ld];
-      const float f = to_tf32((float)v);
-      hv[j] = f;
-      lv[j] = split ? to_tf32((float)(v - (double)f)) : 0.0f;
+      split_tf32(v, hv[j], lv[j]);
+      if (!split) lv[j] = 0.0f;
     }
     h = make_float4(hv[0], hv[1], hv[2], hv[3]);
     l = make_float4(lv[0], lv[1], lv[2], lv[3]);
@@ -256,13 +309,14 @@ __global__ void __launch_bounds__(tc::NTHREADS) k_gemm_tc(const GemmTask* __rest
       float v[32];
       tc::tmem_ld32(lane_addr + c0, v);
       if (row < t.M) {
+        const bool plain = (t.alpha == 1.0 && t.beta == 0.0);  // the Schur product: C = S
 #pragma unroll
         for (int j = 0; j < 32; j++) {
           const int col = tl.n0 + c0 + j;
           if (col < t.N) {
             double* c = t.C + row + (long long)col * t.ldc;
-            const double s = (double)v[j];
-            *c = (t.beta == 0.0) ? t.alpha * s : t.beta * (*c) + t.alpha * s;
+            const double s = widen(v[j]);
+            *c = plain ? s : ((t.beta == 0.0) ? t.alpha * s : t.beta * (*c) + t.alpha * s);
           }
         }
       }

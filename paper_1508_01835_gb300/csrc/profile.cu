@@ -96,6 +96,7 @@ void start() {
   std::lock_guard<std::mutex> g(mu);
   if (on) drain();
   stats.clear();
+  svd_jacobi_flops_take();
   launches_at_start = launches_total();
   on = true;
 }
@@ -104,6 +105,11 @@ int stop(ifmm_kernel_stat* out, int capacity) {
   std::lock_guard<std::mutex> g(mu);
   drain();
   on = false;
+  {
+    auto it = stats.find("k_svd_left");
+    const double jf = (double)svd_jacobi_flops_take();
+    if (it != stats.end()) it->second.flops += jf;
+  }
   Stat& all = stats["(all launches)"];
   all.launches = (long long)(launches_total() - launches_at_start);
   int n = 0;
