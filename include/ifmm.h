@@ -262,8 +262,9 @@ ifmm_status ifmm_server_register(ifmm_server* srv, ifmm_system* sys, ifmm_factor
  * N x nrhs column-major (ld N), 1 <= nrhs <= 32; both must stay valid until
  * the ticket is waited for.  Residual target tol (a block uses the smallest
  * tol and the largest maxit of its requests).  Load shedding: if the system
- * already has 128 columns queued the request is refused with IFMM_ERR_BUDGET
- * (and counted as shed). */
+ * already has a full block (32 columns) queued behind the one in flight, the
+ * request is refused with IFMM_ERR_BUDGET (and counted as shed); this bounds
+ * the queueing delay to about one block's solve time. */
 ifmm_status ifmm_server_submit(ifmm_server* srv, int id, const double* b_host, double* x_host,
                                int nrhs, double tol, int maxit, long long* ticket);
 /* Waits up to timeout_ms (< 0: no limit) for a ticket; IFMM_ERR_TIMEOUT if it

@@ -116,7 +116,7 @@ struct ifmm_server {
   int device = 0;
   size_t budget = 0, used = 0;
   int col_cap = 32;
-  int queue_cap = 128;  // queued columns per system beyond which requests are shed
+  int queue_cap = 32;  // queued columns per system (one block) beyond which requests are shed
   long long shed = 0;
   std::deque<Entry> systems;  // stable references while workers hold one
   std::map<long long, std::unique_ptr<Request>> reqs;
@@ -132,6 +132,8 @@ struct ifmm_server {
     using namespace ifmm;
     cudaStream_t ws = nullptr;
     Arena buf;
+    Arena gws;  // GMRES workspace, reused block after block
+    gws.chunk_bytes = size_t(256) << 20;
     size_t buf_cols = 0;
     long long buf_n = 0;
     double *db = nullptr, *dx = nullptr;
@@ -197,7 +199,7 @@ struct ifmm_server {
           tol = std::min(tol, r->tol);
           maxit = std::max(maxit, r->maxit);
         }
-        gmres_run(E.sys, E.fac, IFMM_MV_FMM, db, dx, width, N, tol, maxit, reps.data(), ws);
+        gmres_run(E.sys, E.fac, IFMM_MV_FMM, db, dx, width, N, tol, maxit, reps.data(), ws, &gws);
         off = 0;
         for (Request* r : batch) {
           CK(cudaMemcpyAsync(r->x, dx + off * N, sizeof(double) * N * r->nrhs,
@@ -234,6 +236,7 @@ struct ifmm_server {
     }
     lk.unlock();
     buf.release();
+    gws.release();
     if (ws) cudaStreamDestroy(ws);
   }
 };

@@ -75,5 +75,5 @@ void factor_solve(ifmm_factorization* f, const double* b, long long ldb, double*
                   long long ldx, int nrhs, cudaStream_t s);
 ifmm_status gmres_run(ifmm_system* sys, ifmm_factorization* fac, int mode, const double* b,
                       double* x, int nrhs, long long ld, double tol, int maxit,
-                      ifmm_gmres_report* rep, cudaStream_t s);
+                      ifmm_gmres_report* rep, cudaStream_t s, Arena* workspace = nullptr);
 }  // namespace ifmm

@@ -127,11 +127,16 @@ static inline int gblocks(long long n) { return (int)std::min<long long>(1024, (
 
 ifmm_status gmres_run(ifmm_system* sys, ifmm_factorization* fac, int mode, const double* b,
                       double* x, int nrhs, long long ld, double tol, int maxit,
-                      ifmm_gmres_report* rep, cudaStream_t s) {
+                      ifmm_gmres_report* rep, cudaStream_t s, Arena* workspace) {
   const long long N = sys->N;
   const int m = maxit;
-  Arena ar;
-  ar.chunk_bytes = size_t(64) << 20;
+  // workspace: the caller's arena, rewound and reused across calls (no device
+  // allocation once it has grown, so no implicit device-wide synchronisation
+  // of cudaMalloc / cudaFree between concurrent solves), or a private one
+  Arena own;
+  own.chunk_bytes = size_t(64) << 20;
+  Arena& ar = workspace ? *workspace : own;
+  ar.reset();
   // Krylov basis: chunks of KCH vectors (ld N * KCH between right-hand sides)
   const long long ldV = N * KCH;
   const int nchunks = m / KCH + 1;
