@@ -7,10 +7,11 @@ any size and on outputs the oracle computes row by row:
   algorithm) and with the timed one (split-TF32 Schur products, symmetric
   variant); the two solutions agree to what that residual allows;
 * sampled rows of the DIRECT product equal the oracle's kernel rows
-  (Sec. 3.1) to the rounding of an N-term FP64 sum, and sampled rows of the FMM product (the operator
-  A_n GMRES solves with, Sec. 3.2) stay within the Chebyshev interpolation
-  error of n = 4 (about 5e-4 relative for this point distribution, measured
-  with the oracle's FMM at N = 8192);
+  (Sec. 3.1) to the rounding of an N-term FP64 sum, and sampled rows of the
+  FMM product (the operator A_n GMRES solves with, Sec. 3.2) stay within the
+  Chebyshev interpolation error of n = 4 on each row's absolute scale
+  sum_j |a_ij x_j| (the oracle's FMM at N = 8192 differs from the kernel by
+  about 5e-4 of ||A x|| for a random x);
 * every rank respects the n^D cap and the top system is no larger than
   64 boxes x 64.
 """
@@ -73,7 +74,13 @@ def test_bench_workload_full_size(ctx):
                 # two FP64 sums of N terms in different orders: each is within
                 # about u sqrt(N) sum_j |a_ij x_j| of the exact row (u = 2^-53)
                 assert np.all(np.abs(yd[rows] - exact) <= 4 * 2.0 ** -53 * np.sqrt(w.N) * scale)
-                assert rel(yf[rows], exact) < 2e-3
+                # the FMM differs from the kernel by the Chebyshev interpolation
+                # error of each far-field entry: bounded on the row's absolute
+                # scale (the solution x cancels A's smooth part, so |A x| itself
+                # is far smaller than that scale)
+                ratio = np.max(np.abs(yf[rows] - exact) / scale)
+                print(f"FMM rows: max |A_n x - A x| / sum|a x| = {ratio:.2e}")
+                assert ratio < 1e-3
         finally:
             ifmm.ifmm_system_destroy(sys)
     # both residuals are <= 1e-10; kappa(A_n) is ~ 1.5e3 here (largest eigenvalue ~ N
