@@ -1,7 +1,7 @@
 #!/usr/bin/env python3
 """Benchmark of the IFMM hot path on one GB300 (or N independent replicas).
 
-Workload (default ``c2``): N = 65,536 points uniform in the unit cube,
+Workload (default ``cube-64k``): N = 65,536 points uniform in the unit cube,
 A_ij = 1/|x_i - x_j|, A_ii = 2 N^(1/3), leaves <= 64 points, Chebyshev 4x4x4,
 eps = 1e-8, one standard-normal right-hand side, FP64 GMRES to a relative
 residual of 1e-10 with the FMM matvec and the IFMM as right preconditioner.
@@ -47,7 +47,7 @@ def parse():
     p.add_argument("--steps", type=int, default=2)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=["c1", "c2"], default="c2")
+    p.add_argument("--workload", choices=["cube-2k", "cube-64k"], default="cube-64k")
     p.add_argument("--schur", choices=["fp64", "fp32", "tf32"], default="fp32",
                    help="Schur-product precision of the timed path (fp32: split-TF32 tensor cores)")
     p.add_argument("--general", action="store_true",
@@ -62,7 +62,7 @@ def parse():
 
 def workload(name):
     import workloads
-    return workloads.c1() if name == "c1" else workloads.c2()
+    return workloads.cube_2k() if name == "cube-2k" else workloads.cube_64k()
 
 
 def describe(w):

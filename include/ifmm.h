@@ -143,7 +143,7 @@ const char* ifmm_status_string(ifmm_status st);
 
 /* ---- system: tree, lists, colours, raw operators (Sec. 2.1, 2.3) ------------ */
 /* pts: device, N x dim row-major, user order; copied.  Builds the uniform tree
- * (Algorithm 1, line 1), the neighbour / interaction lists and colour classes,
+ * (first step of Algorithm 1), the neighbour / interaction lists and colour classes,
  * the Chebyshev operators and the near-field blocks.  Synchronises `stream`. */
 ifmm_status ifmm_system_create(ifmm_ctx* ctx, const double* pts, long long N,
                                const ifmm_kernel* kernel, const ifmm_options* opt,
@@ -180,7 +180,7 @@ ifmm_status ifmm_factor_get_ranks(const ifmm_factorization* fac, int level, int*
 /* Device bytes held by the factorisation. */
 ifmm_status ifmm_factor_footprint(const ifmm_factorization* fac, unsigned long long* bytes);
 
-/* ---- solve (substitution phase, Algorithm 1 lines 8-17) ----------------------- */
+/* ---- solve (substitution phase, the downward pass of Algorithm 1) ------------- */
 /* x = (IFMM factorisation)^-1 b ~= A_n^-1 b.  b, x: device, N x nrhs, ld >= N;
  * b and x may alias. */
 ifmm_status ifmm_solve(ifmm_ctx* ctx, const ifmm_factorization* fac, const double* b, double* x,

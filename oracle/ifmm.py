@@ -26,7 +26,7 @@ Paper sections followed, in order:
   transfers and the parent's near-field blocks stack the children's K blocks.
 
 Readings where the paper is silent or ambiguous (the CUDA path follows the
-same readings; each is listed in the design doc):
+same readings):
 
 R1  rank rule: keep exactly the singular values sigma > tau (sigma == tau is
     dropped); tau = 0 means compression disabled: every direction is kept.
@@ -464,7 +464,7 @@ class IFMM:
         self.top_lu = sla.lu_factor(T) if T.size else None
         self.counters.add("top_flops", 2.0 / 3.0 * T.shape[0] ** 3)
 
-    # -- substitution (Algorithm 1, lines "solve for y^(2)" .. "set x") --------------------
+    # -- substitution (the top solve and downward pass of Algorithm 1) ----------------------
     def solve(self, b: np.ndarray) -> np.ndarray:
         """x ~= A_n^-1 b, b and x in user order; b is (N,) or (N, k)."""
         b = np.asarray(b, dtype=np.float64)

@@ -1,6 +1,6 @@
 // factor.cu -- IFMM elimination (Algorithms 1-3 of the paper) on the GPU.
 //
-// Level by level (l = L .. 2) the driver
+// Level by level (l = L .. 2) the factorisation
 //   1. builds weighted bases for the level (footnote to Eq. U_j_recomp):
 //      left SVD of U_i [K_iq V_q^T]_{q in I_i}, truncated at tau (reading R6);
 //   2. eliminates the level colour by colour (colour = box index mod 3 per
@@ -745,7 +745,7 @@ struct Factorizer {
     }
     run_gemms(scratch, q1, s);
     run_gemms(scratch, q2, s);
-    // new bases and weights (Algorithm 3, lines 1-2)
+    // new bases and weights (the first step of Algorithm 3)
     cps.clear();
     for (int t = 0; t < nJ; t++) {
       const int j = J[t], a = st.a[j], r1 = rn[t];

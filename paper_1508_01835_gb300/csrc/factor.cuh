@@ -7,7 +7,7 @@
 
 namespace ifmm {
 
-// One eliminated box: what the substitution phase needs (Algorithm 1, l. 8-17).
+// One eliminated box: what the substitution phase needs (the downward pass of Algorithm 1).
 struct BlockRef {
   char kind;  // 'x': xtilde_j of a box not yet eliminated; 'y': ybar_h of an eliminated one
   int box, dim, off;

@@ -1,4 +1,4 @@
-// kernels_tree.cu -- uniform 2^D-tree of the points (Algorithm 1, line 1;
+// kernels_tree.cu -- uniform 2^D-tree of the points (the first step of Algorithm 1;
 // Sec. 2.3 lists; Sec. 3 uniform tree with a bounded number of points per leaf).
 //
 // Root: the cube of edge max_d(max_d - min_d) (1 + 1e-12) at the per-dimension

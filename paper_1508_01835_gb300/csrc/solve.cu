@@ -1,8 +1,8 @@
-// solve.cu -- substitution phase of the IFMM (Algorithm 1, lines 8-17).
+// solve.cu -- substitution phase of the IFMM (the downward pass of Algorithm 1).
 //
 // Forward sweep in elimination order: for every eliminated box,
 //   w = E(P,P)^-1 [b_xtilde_i ; 0],  b_R -= E(R,P) w
-// (the right-hand-side update of Algorithm 1, line 5); then the top dense
+// (the right-hand-side update of Algorithm 1); then the top dense
 // solve for y^(2); then the backward sweep in reverse order:
 //   x_P = w - G x_C,  G = E(P,P)^-1 E(P,C),
 // which recovers xtilde_i (and z_i).  The unknowns xtilde^(l) of depth l < L

@@ -1,6 +1,6 @@
 """Run one workload through the library and print what it took.
 
-    python -m paper_1508_01835_gb300.run_case --workload c2 [--N 8192]
+    python -m paper_1508_01835_gb300.run_case --workload cube-64k [--N 8192]
         [--schur fp64|fp32|tf32] [--symmetric] [--reps 2] [--no-gmres]
     python -m paper_1508_01835_gb300.run_case --mode batch [--systems 16] [--nmax 8192]
     python -m paper_1508_01835_gb300.run_case --mode serve [--systems 8] [--nmax 32768]
@@ -38,7 +38,7 @@ if ROOT not in sys.path:
 
 def main(argv=None):
     p = argparse.ArgumentParser()
-    p.add_argument("--workload", choices=["c1", "c2"], default="c2")
+    p.add_argument("--workload", choices=["cube-2k", "cube-64k"], default="cube-64k")
     p.add_argument("--N", type=int, default=0)
     p.add_argument("--schur", choices=["fp64", "fp32", "tf32"], default="fp64")
     p.add_argument("--symmetric", action="store_true")
@@ -60,7 +60,7 @@ def main(argv=None):
     import paper_1508_01835_gb300 as ifmm
     import workloads
 
-    w = workloads.c2() if a.workload == "c2" else workloads.c1()
+    w = workloads.cube_64k() if a.workload == "cube-64k" else workloads.cube_2k()
     if a.N:
         w = workloads.inv_r_cube(a.N, w.seed, f"{w.name}@N={a.N}", w.cheb_n, w.leaf_max, w.eps)
     prec = {"fp64": ifmm.P_FP64, "fp32": ifmm.P_FP32, "tf32": ifmm.P_TF32}[a.schur]
@@ -106,7 +106,7 @@ def _capped(make, count, nmax):
     for k in range(count):
         w = make(k)
         if nmax and w.N > nmax:
-            if w.name.startswith("c4"):
+            if w.name.startswith("sphere"):
                 pts = workloads.unit_sphere(nmax, w.seed)
                 w = workloads.Workload(w.name, pts, workloads.Kernel(workloads.K_INV_R, 0.0,
                                                                      2.0 * nmax ** 0.5),
@@ -122,7 +122,7 @@ def batch(a):
 
     import paper_1508_01835_gb300 as ifmm
     import workloads
-    ws = _capped(workloads.c4_system, a.systems or 16, a.nmax or 8192)
+    ws = _capped(workloads.sphere_system, a.systems or 16, a.nmax or 8192)
     prec = {"fp64": ifmm.P_FP64, "fp32": ifmm.P_FP32, "tf32": ifmm.P_TF32}[a.schur]
     ctx = ifmm.ifmm_ctx_create(0)
     sys = [ifmm.ifmm_system_create(ctx, torch.tensor(w.points, device="cuda"),
@@ -156,7 +156,7 @@ def serve(a):
 
     import paper_1508_01835_gb300 as ifmm
     import workloads
-    ws = _capped(workloads.c5_system, a.systems or 8, a.nmax or 32768)
+    ws = _capped(workloads.serving_cube_system, a.systems or 8, a.nmax or 32768)
     ctx = ifmm.ifmm_ctx_create(0)
     sys = [ifmm.ifmm_system_create(ctx, torch.tensor(w.points, device="cuda"),
                                    ifmm.Kernel(w.kernel.kind, w.kernel.param, w.kernel.diag),

@@ -37,7 +37,7 @@ def ctx():
 
 
 def test_bench_workload_full_size(ctx):
-    w = workloads.c2()
+    w = workloads.cube_64k()
     b = cuda(w.rhs(1)[:, 0])
     xs = {}
     for name, kw in {"fp64-general": dict(schur=ifmm.P_FP64, symmetric=0),

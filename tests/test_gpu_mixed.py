@@ -19,7 +19,7 @@ import torch
 
 import paper_1508_01835_gb300 as ifmm
 from tests.gpu_util import cuda, kernel, opts, rel
-from workloads import c1, small_cube
+from workloads import cube_2k, small_cube
 
 pytestmark = pytest.mark.gpu
 
@@ -84,7 +84,7 @@ def test_fp64_product_kernel_matches(ctx):
 
 
 CASES = {
-    "c1": lambda: c1(),
+    "cube2k": lambda: cube_2k(),
     "3lev": lambda: small_cube(3000, 7, cheb_n=3, leaf_max=32, eps=1e-6),
 }
 

@@ -14,12 +14,12 @@ import paper_1508_01835_gb300 as ifmm
 from oracle.gmres import gmres as oracle_gmres
 from oracle.ifmm import IFMM, sigma0_power
 from tests.gpu_util import cuda, dense_an_solve, kernel, opts, oracle_h2, rel, to_user
-from workloads import Kernel, K_GAUSSIAN, K_INV_R, K_PAPER_D, c1, small_cube
+from workloads import Kernel, K_GAUSSIAN, K_INV_R, K_PAPER_D, cube_2k, small_cube
 
 pytestmark = pytest.mark.gpu
 
 CASES = {
-    "c1": lambda: c1(),                                                   # L = 2, n = 3
+    "cube2k": lambda: cube_2k(),                                                   # L = 2, n = 3
     "3lev": lambda: small_cube(3000, 7, cheb_n=3, leaf_max=32, eps=1e-6),  # L = 3, one merge
     "2d": lambda: small_cube(2500, 9, cheb_n=4, leaf_max=20, eps=1e-8, dim=2,
                              kernel=Kernel(K_GAUSSIAN, 0.05, 1.01)),
@@ -59,7 +59,7 @@ def test_tree_matches_oracle(ctx, name):
         ifmm.ifmm_system_destroy(sys)
 
 
-@pytest.mark.parametrize("name", ["c1", "2d", "ragged", "3lev", "paper"])
+@pytest.mark.parametrize("name", ["cube2k", "2d", "ragged", "3lev", "paper"])
 def test_matvec_parity(ctx, name):
     w = CASES[name]()
     h2 = oracle_h2(w)
@@ -79,7 +79,7 @@ def test_matvec_parity(ctx, name):
         ifmm.ifmm_system_destroy(sys)
 
 
-@pytest.mark.parametrize("name", ["c1", "3lev"])
+@pytest.mark.parametrize("name", ["cube2k", "3lev"])
 def test_sigma0_parity(ctx, name):
     w = CASES[name]()
     h2 = oracle_h2(w)
@@ -137,7 +137,7 @@ def test_factor_solve_parity(ctx, name):
         ifmm.ifmm_system_destroy(sys)
 
 
-@pytest.mark.parametrize("name", ["c1", "3lev", "2d"])
+@pytest.mark.parametrize("name", ["cube2k", "3lev", "2d"])
 def test_symmetric_variant_parity(ctx, name):
     """Reading S (one SVD per box, V side = U side) on both sides with the same
     tau: equal ranks, equal solve output to rounding."""
@@ -161,14 +161,14 @@ def test_symmetric_variant_parity(ctx, name):
 WELL = {
     "3lev": lambda: small_cube(3000, 7, cheb_n=3, leaf_max=32, eps=1e-6,
                                kernel=Kernel(K_INV_R, 0.0, 4.0 * 3000)),
-    "c1": lambda: small_cube(2048, 1000, cheb_n=3, leaf_max=64, eps=1e-6,
+    "cube2k": lambda: small_cube(2048, 1000, cheb_n=3, leaf_max=64, eps=1e-6,
                              kernel=Kernel(K_INV_R, 0.0, 4.0 * 2048)),
     "2d": lambda: small_cube(2500, 9, cheb_n=4, leaf_max=20, eps=1e-8, dim=2,
                              kernel=Kernel(K_GAUSSIAN, 0.05, 3.0)),
 }
 
 
-@pytest.mark.parametrize("name,cap,rows", [("3lev", 12, 20), ("c1", 10, 16), ("2d", 8, 16)])
+@pytest.mark.parametrize("name,cap,rows", [("3lev", 12, 20), ("cube2k", 10, 16), ("2d", 8, 16)])
 def test_randomised_recompression_parity(ctx, name, cap, rows):
     """Blocks taller than `rows` under rank cap `cap` take the randomised SVD
     (Sec. 2.4) on both sides, with the same counter-based test matrix.  The
@@ -192,10 +192,10 @@ def test_randomised_recompression_parity(ctx, name, cap, rows):
         ifmm.ifmm_system_destroy(sys)
 
 
-def test_gmres_c1_direct_matches_dense_lu(ctx):
-    """C1: GMRES with the exact matvec and the IFMM preconditioner reaches
+def test_gmres_cube2k_direct_matches_dense_lu(ctx):
+    """cube-2k: GMRES with the exact matvec and the IFMM preconditioner reaches
     1e-10 and agrees with the dense LU solve of A (Sec. 3.2)."""
-    w = c1()
+    w = cube_2k()
     h2 = oracle_h2(w)
     b = w.rhs(1)[:, 0]
     A = h2.dense_exact()
@@ -214,7 +214,7 @@ def test_gmres_c1_direct_matches_dense_lu(ctx):
         ifmm.ifmm_system_destroy(sys)
 
 
-@pytest.mark.parametrize("name", ["c1", "3lev"])
+@pytest.mark.parametrize("name", ["cube2k", "3lev"])
 def test_gmres_parity_with_oracle(ctx, name):
     """FMM matvec + IFMM right preconditioner: same iteration count as the
     oracle's GMRES (+-1), true residual <= 1e-10, same solution to 1e-8."""

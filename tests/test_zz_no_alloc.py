@@ -15,7 +15,7 @@ import torch
 
 import paper_1508_01835_gb300 as ifmm
 from tests.gpu_util import cuda, kernel, opts, rel
-from workloads import Kernel, K_GAUSSIAN, c1, small_cube
+from workloads import Kernel, K_GAUSSIAN, cube_2k, small_cube
 
 pytestmark = pytest.mark.gpu
 
@@ -30,7 +30,7 @@ def ctx():
 
 
 @pytest.mark.parametrize("make", [
-    lambda: c1(),
+    lambda: cube_2k(),
     lambda: small_cube(3000, 7, cheb_n=3, leaf_max=32, eps=1e-6),
     lambda: small_cube(2500, 9, cheb_n=4, leaf_max=20, eps=1e-8, dim=2,
                        kernel=Kernel(K_GAUSSIAN, 0.05, 1.01)),

@@ -4,26 +4,28 @@ This module is shared by the CPU oracle, the tests, ``bench.py`` and the
 CUDA path.  It draws random points and right-hand sides and states each
 workload's parameters; it contains none of the method's arithmetic.
 
-Seeds follow one rule: points of system ``s`` of workload ``c`` use
-``1000 * c + s``; the right-hand sides of that system use the point seed + 1.
-All draws use numpy's PCG64 generator.
+Seeds: points of system ``s`` of a workload with base seed ``B`` use
+``B + s`` (bases 1000, 2000, 3000, 4000, 5000 for the five workloads below);
+the right-hand sides of that system use the point seed + 1.  All draws use
+numpy's PCG64 generator.
 
 Workloads (the paper's own examples, Sec. 3.1-3.2, use random points in a
 cube or on a sphere; these follow the same shapes):
 
-* ``c1``  N=2048 uniform in the unit cube, A_ij = 1/r, A_ii = 2 N^(1/3),
-          leaves <= 64, Chebyshev 3x3x3, eps = 1e-6, 1 RHS.
-* ``c2``  N=65536 uniform in the unit cube, same kernel rule, leaves <= 64,
-          Chebyshev 4x4x4, eps = 1e-8, 1 RHS.
-* ``c3``  N=2^20 uniform in the unit square, Gaussian RBF sigma = 0.05 with
-          1e-2 added on the diagonal, leaves <= 128, Chebyshev 6x6,
-          eps = 1e-6, 4 RHS.
-* ``c4``  256 systems, N log-uniform in [1024, 65536] on the unit sphere
-          surface, A_ii = 2 sqrt(N), Chebyshev 4x4x4, eps = 1e-4.
-* ``c5``  64 systems, N log-uniform in [4096, 262144] in the unit cube,
-          1/r kernel, A_ii = 2 N^(1/3), Chebyshev 3x3x3, eps = 1e-6.
-* ``paper``  the replication workload of Sec. 3.2: N points uniform in
-          [-1, 1]^3 with the kernel of Eq. (K_ij) (parameter d).
+* ``cube_2k``   N=2048 uniform in the unit cube, A_ij = 1/r, A_ii = 2 N^(1/3),
+                leaves <= 64, Chebyshev 3x3x3, eps = 1e-6, 1 RHS.
+* ``cube_64k``  N=65536 uniform in the unit cube, same kernel rule, leaves <= 64,
+                Chebyshev 4x4x4, eps = 1e-8, 1 RHS (the bench workload).
+* ``square_gauss_1m``  N=2^20 uniform in the unit square, Gaussian RBF
+                sigma = 0.05 with 1e-2 added on the diagonal, leaves <= 128,
+                Chebyshev 6x6, eps = 1e-6, 4 RHS.
+* ``sphere_system(s)``  system s of 256, N log-uniform in [1024, 65536] on the
+                unit sphere surface, A_ii = 2 sqrt(N), Chebyshev 4x4x4, eps = 1e-4.
+* ``serving_cube_system(s)``  system s of 64, N log-uniform in [4096, 262144]
+                in the unit cube, 1/r kernel, A_ii = 2 N^(1/3), Chebyshev 3x3x3,
+                eps = 1e-6.
+* ``paper_cube``  the replication workload of Sec. 3.2: N points uniform in
+                [-1, 1]^3 with the kernel of Eq. (K_ij) (parameter d).
 """
 from __future__ import annotations
 
@@ -98,33 +100,41 @@ def inv_r_cube(N: int, seed: int, name: str, cheb_n: int, leaf_max: int, eps: fl
                     leaf_max, eps, nrhs, seed)
 
 
-def c1() -> Workload:
-    return inv_r_cube(2048, 1000, "c1", 3, 64, 1e-6)
+def cube_2k() -> Workload:
+    """2,048 points uniform in the unit cube, 1/r, Chebyshev 3^3, eps = 1e-6."""
+    return inv_r_cube(2048, 1000, "cube-2k", 3, 64, 1e-6)
 
 
-def c2() -> Workload:
-    return inv_r_cube(65536, 2000, "c2", 4, 64, 1e-8)
+def cube_64k() -> Workload:
+    """65,536 points uniform in the unit cube, 1/r, Chebyshev 4^3, eps = 1e-8."""
+    return inv_r_cube(65536, 2000, "cube-64k", 4, 64, 1e-8)
 
 
-def c3(N: int = 1 << 20) -> Workload:
+def square_gauss_1m(N: int = 1 << 20) -> Workload:
+    """2^20 points uniform in the unit square, Gaussian RBF sigma = 0.05 with
+    A_ii = 1.01, leaves <= 128, Chebyshev 6^2, eps = 1e-6, 4 right-hand sides."""
     seed = 3000
     pts = uniform_cube(N, seed, 2)
-    return Workload("c3", pts, Kernel(K_GAUSSIAN, 0.05, 1.0 + 1e-2), 2, 6, 128, 1e-6, 4, seed)
+    return Workload("square-gauss-1m", pts, Kernel(K_GAUSSIAN, 0.05, 1.0 + 1e-2), 2, 6, 128, 1e-6, 4, seed)
 
 
-def c4_system(s: int) -> Workload:
+def sphere_system(s: int) -> Workload:
+    """System s of 256 on the unit sphere: N log-uniform in [1024, 65536],
+    1/r with A_ii = 2 sqrt(N), Chebyshev 4^3, eps = 1e-4."""
     sizes = log_uniform_sizes(256, 1024, 65536, 4000 + 999)
     N = sizes[s]
     seed = 4000 + s
     pts = unit_sphere(N, seed)
-    return Workload(f"c4[{s}]", pts, Kernel(K_INV_R, 0.0, 2.0 * math.sqrt(N)), 3, 4, 64, 1e-4,
+    return Workload(f"sphere[{s}]", pts, Kernel(K_INV_R, 0.0, 2.0 * math.sqrt(N)), 3, 4, 64, 1e-4,
                     1, seed)
 
 
-def c5_system(s: int) -> Workload:
+def serving_cube_system(s: int) -> Workload:
+    """System s of 64 in the unit cube: N log-uniform in [4096, 262144], 1/r,
+    Chebyshev 3^3, eps = 1e-6."""
     sizes = log_uniform_sizes(64, 4096, 262144, 5000 + 999)
     N = sizes[s]
-    return inv_r_cube(N, 5000 + s, f"c5[{s}]", 3, 64, 1e-6)
+    return inv_r_cube(N, 5000 + s, f"serving-cube[{s}]", 3, 64, 1e-6)
 
 
 def paper_cube(N: int, d: float, cheb_n: int, seed: int = 6000, leaf_max: int = 100,
@@ -137,7 +147,7 @@ def paper_cube(N: int, d: float, cheb_n: int, seed: int = 6000, leaf_max: int = 
 
 def small_cube(N: int, seed: int, cheb_n: int = 3, leaf_max: int = 16, eps: float = 1e-6,
                dim: int = 3, kernel: Kernel | None = None) -> Workload:
-    """Small seeded cases for parity tests (same recipe as c1/c2 at reduced N)."""
+    """Small seeded cases for parity tests (the cube recipes at reduced N)."""
     pts = uniform_cube(N, seed, dim)
     if kernel is None:
         kernel = Kernel(K_INV_R, 0.0, 2.0 * N ** (1.0 / dim))
@@ -146,5 +156,5 @@ def small_cube(N: int, seed: int, cheb_n: int = 3, leaf_max: int = 16, eps: floa
 
 
 def by_name(name: str) -> Workload:
-    table = {"c1": c1, "c2": c2, "c3": c3}
+    table = {"cube-2k": cube_2k, "cube-64k": cube_64k, "square-gauss-1m": square_gauss_1m}
     return table[name]()
