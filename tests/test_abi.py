@@ -29,7 +29,10 @@ def lib():
 def test_header_declares_the_boundary():
     names = declared_functions()
     for must in ("ifmm_factor", "ifmm_solve", "fmm_matvec", "gmres_solve", "ifmm_system_create",
-                 "ifmm_sigma0", "gmres_solve_host"):
+                 "ifmm_sigma0", "gmres_solve_host", "ifmm_factor_batch", "ifmm_server_create",
+                 "ifmm_server_register", "ifmm_server_submit", "ifmm_server_wait",
+                 "ifmm_server_stats", "ifmm_server_destroy", "ifmm_schur_product",
+                 "fmm_matvec_static"):
         assert must in names
 
 
@@ -47,6 +50,15 @@ def test_status_strings_and_argument_checks(lib):
     assert lib.ifmm_factor(None, None, None, None) == 1
     out = ctypes.c_void_p()
     assert lib.ifmm_ctx_create(-1, ctypes.byref(out)) == 1
+    # the many-systems and product entry points validate before touching CUDA
+    assert lib.ifmm_factor_batch(None, None, 0, None, None) == 1
+    assert lib.ifmm_server_create(None, 0, 0, ctypes.byref(out)) == 1
+    assert lib.ifmm_server_submit(None, 0, None, None, 1, 1e-10, 10, None) == 1
+    assert lib.ifmm_server_wait(None, 1, 0, None, None) == 1
+    assert lib.ifmm_server_stats(None, None, None, None, None) == 1
+    assert lib.ifmm_schur_product(None, 0, 1, 1, 1, None, 1, 0, None, 1, 0, None, 1,
+                                  1.0, 0.0, None) == 1
+    assert lib.fmm_matvec_static(None, None, None, None, 1, 10, None) == 1
 
 
 def test_product_path_fails_loudly_without_library(tmp_path, monkeypatch):
