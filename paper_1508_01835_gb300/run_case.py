@@ -5,6 +5,8 @@
     python -m paper_1508_01835_gb300.run_case --mode batch [--systems 16] [--nmax 8192]
     python -m paper_1508_01835_gb300.run_case --mode serve [--systems 8] [--nmax 32768]
         [--rate 200] [--seconds 10]
+    python -m paper_1508_01835_gb300.run_case --mode paper [--d 1e-3] [--orders 1,2,3,4]
+        [--fmm-n 5] [--N 100000]
 
 Each repetition: system creation (tree, lists, operators), factorisation
 (sigma_0, weighted bases, elimination, top LU) and FMM-GMRES to 1e-10 on one
@@ -44,7 +46,10 @@ def main(argv=None):
     p.add_argument("--symmetric", action="store_true")
     p.add_argument("--reps", type=int, default=2)
     p.add_argument("--no-gmres", action="store_true")
-    p.add_argument("--mode", choices=["case", "batch", "serve"], default="case")
+    p.add_argument("--mode", choices=["case", "batch", "serve", "paper"], default="case")
+    p.add_argument("--d", type=float, default=1e-3)
+    p.add_argument("--orders", default="1,2,3,4")
+    p.add_argument("--fmm-n", type=int, default=5)
     p.add_argument("--systems", type=int, default=0)
     p.add_argument("--nmax", type=int, default=0)
     p.add_argument("--rate", type=float, default=200.0)
@@ -54,6 +59,8 @@ def main(argv=None):
         return batch(a)
     if a.mode == "serve":
         return serve(a)
+    if a.mode == "paper":
+        return paper(a)
 
     import torch
 
@@ -96,6 +103,45 @@ def main(argv=None):
               f"sigma0 {info.seconds_sigma0:.3f} elim {info.seconds_elim:.3f} "
               f"top {info.seconds_top:.3f} bytes {info.factor_bytes / 1e9:.2f}GB", flush=True)
         ifmm.ifmm_factor_destroy(f)
+        ifmm.ifmm_system_destroy(s)
+    ifmm.ifmm_ctx_destroy(ctx)
+
+
+def paper(a):
+    """The experiment of Sec. 3.2 (Table 1 for d = 1e-3, Table 2 for d = 1e-2):
+    N points uniform in [-1, 1]^3 with the kernel of Eq. (K_ij), eps = 1e-3,
+    leaves of at most 100 points, GMRES to 1e-10 with an FMM matvec of fixed
+    order --fmm-n, unpreconditioned and with the IFMM of each order n as right
+    preconditioner (the paper's general algorithm in FP64)."""
+    import torch
+
+    import paper_1508_01835_gb300 as ifmm
+    import workloads
+    N = a.N or 100000
+    ctx = ifmm.ifmm_ctx_create(0)
+    for k, n in enumerate([int(v) for v in a.orders.split(",")] + [0]):
+        w = workloads.paper_cube(N, a.d, max(n, 1))
+        opt = ifmm.make_options(dim=3, cheb_n=max(n, 1), leaf_max=w.leaf_max, eps=w.eps,
+                                fmm_n=a.fmm_n)
+        s = ifmm.ifmm_system_create(ctx, torch.tensor(w.points, device="cuda"),
+                                    ifmm.Kernel(w.kernel.kind, w.kernel.param, w.kernel.diag), opt)
+        b = torch.tensor(w.rhs(1)[:, 0], device="cuda")
+        x = torch.empty_like(b)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        f = ifmm.ifmm_factor(ctx, s) if n > 0 else None
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        reps = ifmm.gmres_solve(ctx, s, f, ifmm.MV_FMM, b, x, w.N, 1e-10, 500)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        info = ifmm.ifmm_system_get_info(s)
+        label = f"IFMM n={n}" if n > 0 else "no preconditioner"
+        print(f"[paper d={a.d:g} N={w.N} L={info.levels} fmm_n={a.fmm_n}] {label}: "
+              f"{reps[0].iters} GMRES iterations, true residual {reps[0].true_rel_residual:.2e}, "
+              f"factor {t1 - t0:.2f}s, GMRES {t2 - t1:.2f}s", flush=True)
+        if f is not None:
+            ifmm.ifmm_factor_destroy(f)
         ifmm.ifmm_system_destroy(s)
     ifmm.ifmm_ctx_destroy(ctx)
 
