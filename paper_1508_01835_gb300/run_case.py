@@ -6,7 +6,7 @@
     python -m paper_1508_01835_gb300.run_case --mode serve [--systems 8] [--nmax 32768]
         [--rate 200] [--seconds 10]
     python -m paper_1508_01835_gb300.run_case --mode paper [--d 1e-3] [--orders 1,2,3,4]
-        [--fmm-n 5] [--N 100000]
+        [--fmm-n 5] [--leaf 100] [--N 100000]
 
 Each repetition: system creation (tree, lists, operators), factorisation
 (sigma_0, weighted bases, elimination, top LU) and FMM-GMRES to 1e-10 on one
@@ -50,6 +50,7 @@ def main(argv=None):
     p.add_argument("--d", type=float, default=1e-3)
     p.add_argument("--orders", default="1,2,3,4")
     p.add_argument("--fmm-n", type=int, default=5)
+    p.add_argument("--leaf", type=int, default=100)
     p.add_argument("--systems", type=int, default=0)
     p.add_argument("--nmax", type=int, default=0)
     p.add_argument("--rate", type=float, default=200.0)
@@ -120,7 +121,7 @@ def paper(a):
     N = a.N or 100000
     ctx = ifmm.ifmm_ctx_create(0)
     for k, n in enumerate([int(v) for v in a.orders.split(",")] + [0]):
-        w = workloads.paper_cube(N, a.d, max(n, 1))
+        w = workloads.paper_cube(N, a.d, max(n, 1), leaf_max=a.leaf)
         opt = ifmm.make_options(dim=3, cheb_n=max(n, 1), leaf_max=w.leaf_max, eps=w.eps,
                                 fmm_n=a.fmm_n)
         s = ifmm.ifmm_system_create(ctx, torch.tensor(w.points, device="cuda"),
