@@ -228,7 +228,8 @@ ifmm_status gmres_solve_host(ifmm_ctx* ctx, const ifmm_system* sys,
 
 /* ---- many systems: batched factorisation (the paper factorises one system at a
  * time, Algorithm 1; independent systems share nothing) ------------------------ */
-/* Factorises sys[0..count-1] (distinct systems) concurrently: up to 8 worker
+/* Factorises sys[0..count-1] (distinct systems; a repeated handle is
+ * IFMM_ERR_INVALID_ARG) concurrently: up to 8 worker
  * threads, each on its own CUDA stream that first waits for the work queued on
  * `stream`, take the systems largest first.  out: host array of count
  * handles, filled in (each freed by ifmm_factor_destroy).  On any error other
@@ -254,7 +255,8 @@ void ifmm_server_destroy(ifmm_server* srv);
 /* Admits (sys, fac) if its device memory -- operators, factorisation, solve
  * plans and the GMRES workspace of one 32-column block with maxit iterations
  * -- fits what is left of hbm_budget; IFMM_ERR_BUDGET otherwise (nothing is
- * registered).  The server does not own sys or fac; they must outlive it.
+ * registered).  A system or factorisation registered twice is
+ * IFMM_ERR_INVALID_ARG.  The server does not own sys or fac; they must outlive it.
  * *id: the handle for ifmm_server_submit. */
 ifmm_status ifmm_server_register(ifmm_server* srv, ifmm_system* sys, ifmm_factorization* fac,
                                  int maxit, int* id);

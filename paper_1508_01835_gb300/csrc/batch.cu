@@ -246,8 +246,11 @@ extern "C" {
 ifmm_status ifmm_factor_batch(ifmm_ctx* ctx, ifmm_system* const* sys, int count,
                               ifmm_stream stream, ifmm_factorization** out) {
   if (!ctx || count < 0 || (count > 0 && (!sys || !out))) return IFMM_ERR_INVALID_ARG;
-  for (int k = 0; k < count; k++)
+  for (int k = 0; k < count; k++) {
     if (!sys[k]) return IFMM_ERR_INVALID_ARG;
+    for (int q = 0; q < k; q++)  // one worker per system: a system may appear once
+      if (sys[q] == sys[k]) return IFMM_ERR_INVALID_ARG;
+  }
   std::string err;
   ifmm_status st = IFMM_OK;
   try {
@@ -302,6 +305,11 @@ ifmm_status ifmm_server_register(ifmm_server* s, ifmm_system* sys, ifmm_factoriz
   const size_t gm = sizeof(double) * (size_t)sys->N * cols * ((size_t)maxit + 8);
   const size_t bytes = sys->mem.held + fac->store.held + fac->plan_bytes() + gm;
   std::lock_guard<std::mutex> g(s->mu);
+  for (const auto& e : s->systems)
+    if (e.sys == sys || e.fac == fac) {  // a system is served by one worker at a time
+      s->last_error = "this system or factorisation is already registered";
+      return IFMM_ERR_INVALID_ARG;
+    }
   if (s->used + bytes > s->budget) {
     s->last_error = "admission refused: the system needs " + std::to_string(bytes) +
                     " bytes of device memory, " + std::to_string(s->budget - s->used) +

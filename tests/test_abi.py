@@ -52,6 +52,11 @@ def test_status_strings_and_argument_checks(lib):
     assert lib.ifmm_ctx_create(-1, ctypes.byref(out)) == 1
     # the many-systems and product entry points validate before touching CUDA
     assert lib.ifmm_factor_batch(None, None, 0, None, None) == 1
+    # a repeated system handle is refused before the context is touched
+    fake = ctypes.c_void_p(0x1000)
+    two = (ctypes.c_void_p * 2)(0x2000, 0x2000)
+    outs = (ctypes.c_void_p * 2)()
+    assert lib.ifmm_factor_batch(fake, two, 2, None, outs) == 1
     assert lib.ifmm_server_create(None, 0, 0, ctypes.byref(out)) == 1
     assert lib.ifmm_server_submit(None, 0, None, None, 1, 1e-10, 10, None) == 1
     assert lib.ifmm_server_wait(None, 1, 0, None, None) == 1
