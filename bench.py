@@ -304,25 +304,11 @@ def run_ours(args):
                "h2d_bytes_per_step": int(pts_h.nbytes + b_h.nbytes),
                "d2h_bytes_per_step": int(b_h.nbytes)}
 
-    # roofline of the dominant kernel, from the library's own event timings
-    kern_stats = {k: v for k, v in stats.items() if not k.startswith("(") and ":" not in k}
-    dom = max(kern_stats.items(), key=lambda kv: kv[1][1]) if kern_stats else None
-    roofline = None
-    if dom:
-        name, (launches, secs, flops, nbytes) = dom
-        if name == "k_spmm":
-            peak = _measured_peaks().get("hbm_gbs")
-            achieved = nbytes / secs / 1e9
-            roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                        "frac": achieved / peak if peak else None,
-                        "traffic": _traffic(name), "kernel": name, "peak_source": "measured"}
-        else:
-            achieved = flops / secs / 1e12
-            roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                        "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                        "traffic": _traffic(name), "kernel": name,
-                        "peak_source": "FP64 nominal 1.25 TFLOP/s (no measured FP64 figure)",
-                        "launches": launches, "share_of_step": secs / (ms / 1e3)}
+    # rooflines from the library's own event timings: every profiled kernel,
+    # the dominant one, and the time-weighted fraction
+    per_kernel, roofline, weighted = kernel_rooflines(stats, ms / 1e3, _measured_peaks())
+    if roofline:
+        roofline["traffic"] = _traffic(roofline["kernel"])
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -344,7 +330,8 @@ def run_ours(args):
                   for l in range(2, info.levels + 1)},
         "clocks": clk, "e2e": e2e, "roofline": roofline,
         "gpu_launches": int(stats.get("(all launches)", (0,))[0]),
-        "kernels": {k: {"launches": v[0], "s": round(v[1], 4)} for k, v in kern_stats.items()},
+        "kernels": per_kernel,
+        "roofline_time_weighted_frac": weighted,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
@@ -353,6 +340,57 @@ def run_ours(args):
     ifmm.ifmm_ctx_destroy(ctx)
     if dist:
         dist.destroy_process_group()
+
+
+TF32_PER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rates of the platform
+
+
+def kernel_rooflines(stats, step_seconds, peaks):
+    """Per-kernel roofline rows from the library's launch profile.
+
+    stats: {name: (launches, seconds, flops, bytes)} (ifmm_profile_stop); names
+    starting with "(" or containing ":" are totals or graph replays, not kernels.
+    Bounds: block-row products (k_spmm*) are HBM-bound (bytes against the
+    measured copy bandwidth); the tensor-core Schur products (k_gemm_tc*) are
+    TF32 contractions (algorithmic 2MNK against the measured bf16 rate times
+    the nominal TF32/BF16 ratio; the split mode issues three TF32 products per
+    algorithmic product); everything else is FP64 arithmetic against the
+    nominal FP64 rate.  Returns (rows by name, dominant row, time-weighted frac).
+    """
+    rows = {}
+    for name, (launches, secs, flops, nbytes) in stats.items():
+        if name.startswith("(") or ":" in name or secs <= 0:
+            continue
+        if name.startswith("k_spmm"):
+            peak, unit, bound = peaks.get("hbm_gbs"), "GB/s", "hbm"
+            achieved = nbytes / secs / 1e9
+            src = "measured copy bandwidth"
+        elif name.startswith("k_gemm_tc"):
+            peak = peaks.get("bf16_tflops", 0.0) * TF32_PER_BF16
+            unit, bound = "TFLOP/s", "tensor"
+            achieved = flops / secs / 1e12
+            src = "measured bf16 x nominal TF32/BF16 ratio" + (
+                "; three TF32 products per algorithmic product" if "3x" in name else "")
+        else:
+            peak, unit, bound = FP64_PEAK_TFLOPS, "TFLOP/s", "alu"
+            achieved = flops / secs / 1e12
+            src = "FP64 nominal 1.25 TFLOP/s (no measured FP64 figure)"
+        rows[name] = {"launches": int(launches), "s": round(secs, 4),
+                      "share_of_step": secs / step_seconds if step_seconds > 0 else None,
+                      "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                      "frac": achieved / peak if peak else None, "peak_source": src}
+    dominant = None
+    if rows:
+        name = max(rows, key=lambda k: rows[k]["s"])
+        r = rows[name]
+        dominant = {"bound": r["bound"], "achieved": r["achieved"], "peak": r["peak"],
+                    "unit": r["unit"], "frac": r["frac"], "traffic": None, "kernel": name,
+                    "peak_source": r["peak_source"], "launches": r["launches"],
+                    "share_of_step": r["share_of_step"]}
+    timed = [(r["s"], r["frac"]) for r in rows.values() if r["frac"] is not None]
+    total = sum(t for t, _ in timed)
+    weighted = sum(t * f for t, f in timed) / total if total > 0 else None
+    return rows, dominant, weighted
 
 
 def max_over_ranks(ms, dist, device):
@@ -382,8 +420,9 @@ def _measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             return json.load(f)
-    except OSError:
-        return {"hbm_gbs": 6800.0}
+    except (OSError, ValueError):
+        # the platform's fallback figures (one earlier measurement on a GB300)
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "fallback": True}
 
 
 def _traffic(kernel):

@@ -1,0 +1,37 @@
+"""Host logic of bench.py (no GPU): the roofline rows built from the library's
+launch profile, with the bound chosen per kernel family."""
+import pytest
+
+import bench
+
+PEAKS = {"hbm_gbs": 6685.5, "bf16_tflops": 1944.2}
+
+
+def test_rooflines_per_family_dominant_and_weighted():
+    stats = {  # name: (launches, seconds, flops, bytes)
+        "k_svd_left": (452, 10.0, 1.4e12, 0.0),
+        "k_gemm_tc_3xtf32": (162, 0.8, 4.74e12, 0.0),
+        "k_spmm_job": (40, 0.6, 1e9, 3.0e12),
+        "k_gemm_fp64": (2812, 3.2, 1.6e12, 0.0),
+        "(all launches)": (42822, 0.0, 0.0, 0.0),
+        "graph:ifmm_solve": (20, 0.5, 1e9, 1e9),
+    }
+    rows, dom, weighted = bench.kernel_rooflines(stats, 21.0, PEAKS)
+    assert set(rows) == {"k_svd_left", "k_gemm_tc_3xtf32", "k_spmm_job", "k_gemm_fp64"}
+    assert dom["kernel"] == "k_svd_left" and dom["bound"] == "alu"
+    assert dom["achieved"] == pytest.approx(0.14) and dom["frac"] == pytest.approx(0.14 / 1.25)
+    assert dom["share_of_step"] == pytest.approx(10.0 / 21.0)
+    tc = rows["k_gemm_tc_3xtf32"]
+    assert tc["bound"] == "tensor" and tc["peak"] == pytest.approx(1944.2 * 1.1 / 2.25)
+    assert tc["achieved"] == pytest.approx(4.74e12 / 0.8 / 1e12)
+    sp = rows["k_spmm_job"]
+    assert sp["bound"] == "hbm" and sp["achieved"] == pytest.approx(5000.0)
+    assert sp["frac"] == pytest.approx(5000.0 / 6685.5)
+    fr = [(r["s"], r["frac"]) for r in rows.values()]
+    assert weighted == pytest.approx(sum(t * f for t, f in fr) / sum(t for t, _ in fr))
+
+
+def test_rooflines_empty_profile():
+    rows, dom, weighted = bench.kernel_rooflines({"(all launches)": (0, 0.0, 0.0, 0.0)}, 1.0,
+                                                 PEAKS)
+    assert rows == {} and dom is None and weighted is None
