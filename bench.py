@@ -10,8 +10,12 @@ A step is one pass of the whole path over the synthetic input already resident
 in device memory: tree + lists + colours, operators, sigma_0, weighted bases,
 elimination of every level, top LU, then GMRES (solve sweeps + FMM matvecs).
 ``value`` is solves/s (right-hand sides taken to 1e-10 per second of step).
-``e2e`` repeats the step through the C-ABI host-buffer entry points
-(points and b from host memory, x back to host memory).
+The timed path uses split-TF32 Schur products on the tensor cores and the
+symmetric variant (``--schur``, ``--general`` choose others); the same run
+times one step of the plain FP64 general algorithm on the same input
+(``plain_fp64``: "factor s vs plain FP64").  ``e2e`` repeats the step through
+the C-ABI host-buffer entry points (points and b from host memory, x back to
+host memory).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
