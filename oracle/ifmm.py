@@ -67,9 +67,12 @@ S   symmetric variant (optional; the paper notes that its algorithm is not
 Parity: pinned by tests -- with tau = 0 the factorisation is an exact block
 LU of E and the solve equals the dense solve of A_n to rounding; the
 two-block example of Appendix C gives the printed closed-form matrix; the
-solve error tracks eps; the counted flops and stored bytes grow linearly in
-N.  The exact rank profile at tau > 0 has no printed value to pin against
-(parity unpinned beyond self-consistency and the error bound).
+solve error tracks eps.  The exact rank profile at tau > 0 has no printed
+value to pin against (parity unpinned beyond self-consistency and the error
+bound).  The linear growth of cost and memory in N (Sec. 2.5) is not pinned:
+at the sizes this oracle reaches in seconds (one to three levels) the cost
+is dominated by the first upper level, whose boxes stack eight children's
+ranks, and grows faster than N.
 """
 from __future__ import annotations
 
