@@ -163,8 +163,9 @@ def oracle_sample_step(w_full):
 
 def sample_text(w):
     return (f"the oracle's full pass (tree, operators, sigma_0, factor, GMRES) on the same recipe "
-            f"at N={SAMPLE_N} (seed {w.seed}); solves/s scaled to N={w.N} by the O(N) cost of "
-            f"the method (x{SAMPLE_N}/{w.N})")
+            f"at N={SAMPLE_N} (seed {w.seed}); solves/s scaled to N={w.N} by the method's "
+            f"asymptotic O(N) cost (x{SAMPLE_N}/{w.N}); the oracle's cost grows faster than N "
+            "at these sizes, so the scaled figure overstates it")
 
 
 def cpu_baseline(w):
