@@ -42,9 +42,9 @@ typedef enum {
   IFMM_ERR_CUDA = 3,
   IFMM_ERR_SINGULAR_PIVOT = 4, /* a pivot block E(P,P) had a pivot <= 1e-14 max|E(P,P)| */
   IFMM_ERR_NOT_CONVERGED = 5,  /* GMRES reached maxit above tol (report still filled) */
-  IFMM_ERR_TIMEOUT = 6,
-  IFMM_ERR_BUDGET = 7,
-  IFMM_ERR_UNSUPPORTED = 8
+  IFMM_ERR_TIMEOUT = 6,        /* a bounded device wait ran out, or ifmm_server_wait's limit */
+  IFMM_ERR_BUDGET = 7,         /* server admission refused, or a request shed              */
+  IFMM_ERR_UNSUPPORTED = 8     /* e.g. BF16 Schur products (declared, not implemented)     */
 } ifmm_status;
 
 /* Kernel of the matrix (Sec. 3.1). */
