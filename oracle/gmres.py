@@ -1,10 +1,12 @@
-"""Non-restarted GMRES with a right preconditioner (oracle).
+"""Non-restarted GMRES with a right or left preconditioner (oracle).
 
 Paper: Sec. 3.2 -- the system A x = b is solved by non-restarted GMRES
 (ref. saad86a) with tolerance 1e-10 on the relative residual
 ||b - A x|| / ||b|| and at most 500 iterations; the FMM evaluates the
 products and the IFMM is applied as a right preconditioner.  Appendix B
-compares right with left preconditioning (left is not built here).
+compares right with left preconditioning; with the preconditioner on the
+left, GMRES runs on P^-1 A x = P^-1 b and the tolerance applies to
+||P^-1 b - P^-1 A x|| / ||P^-1 b||.
 
 Readings (the paper does not state them): x_0 = 0; Arnoldi with classical
 Gram-Schmidt applied twice (CGS2); Givens rotations on the Hessenberg
@@ -22,11 +24,19 @@ import math
 import numpy as np
 
 
-def gmres(matvec, b: np.ndarray, precond=None, tol: float = 1e-10, maxit: int = 500):
-    """Returns (x, iterations, relative residual estimate)."""
+def gmres(matvec, b: np.ndarray, precond=None, tol: float = 1e-10, maxit: int = 500,
+          side: str = "right"):
+    """Returns (x, iterations, relative residual estimate).
+
+    side "right": Krylov space of A P^-1, x = P^-1 (V y), estimate of
+    ||b - A x|| / ||b||.  side "left" (Appendix B): Krylov space of P^-1 A
+    started from P^-1 b, x = V y, estimate of ||P^-1 (b - A x)|| / ||P^-1 b||.
+    """
     b = np.asarray(b, dtype=np.float64)
     M = precond if precond is not None else (lambda v: v)
-    beta = float(np.linalg.norm(b))
+    left = side == "left"
+    r0 = M(b) if left else b
+    beta = float(np.linalg.norm(r0))
     n = b.shape[0]
     if beta == 0.0:
         return np.zeros(n), 0, 0.0
@@ -36,11 +46,11 @@ def gmres(matvec, b: np.ndarray, precond=None, tol: float = 1e-10, maxit: int = 
     sn = np.zeros(maxit)
     g = np.zeros(maxit + 1)
     g[0] = beta
-    V[0] = b / beta
+    V[0] = r0 / beta
     k = 0
     res = beta
     for k in range(maxit):
-        w = matvec(M(V[k]))
+        w = M(matvec(V[k])) if left else matvec(M(V[k]))
         h = V[:k + 1] @ w                       # CGS, first pass
         w = w - V[:k + 1].T @ h
         h2 = V[:k + 1] @ w                      # second pass
@@ -69,5 +79,5 @@ def gmres(matvec, b: np.ndarray, precond=None, tol: float = 1e-10, maxit: int = 
     else:
         k = maxit
     y = np.linalg.solve(np.triu(H[:k, :k]), g[:k]) if k else np.zeros(0)
-    x = M(V[:k].T @ y)
+    x = V[:k].T @ y if left else M(V[:k].T @ y)
     return x, k, res / beta

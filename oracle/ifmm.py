@@ -49,14 +49,21 @@ R7  parent bases are initialised after the children's level is eliminated
     (Algorithm 1 lists initialisation first; the parent's U, V depend on the
     children's r_j, t_j of Eqs. U_parent_j_update, V_parent_j_update).
 R8  pivoting: partial (row) pivoting inside E(P, P) only (LAPACK getrf).
-R9  an optional rank cap bounds r (default here: none; the CUDA library's
-    default is n^D, the rank of the initial Chebyshev representation).
-R3b blocks taller than rsvd_rows rows (default 160) that are truncated below
-    their height are recompressed with the randomised SVD of Sec. 2.4 (Halko et
-    al.): k = min(a, cap + 16, 144) columns of a uniform [-1, 1) test matrix
-    drawn from a counter-based SplitMix64 stream (seeded by level, box and
-    side, so the CUDA path draws the same numbers), one power iteration with
-    re-orthonormalisation, and the exact SVD of the projected k-row matrix.
+R9  an optional rank cap bounds r (default: none, the rank rule is tau
+    alone).  Sec. 2.4 names two ways to fix a fill-in's rank: a prescribed
+    rank, or the relative accuracy eps; the cap combines them (the rank at
+    tau, but at most the prescribed rank).
+R3b the randomised SVD of Sec. 2.4 (Halko, Martinsson, Tropp 2011,
+    randomised subspace iteration) is an option, off by default (then the
+    exact truncated SVD of reading R3 is used everywhere).  Its parameters are
+    fixed readings, not tuning knobs: it needs a target rank, so it applies
+    only under a rank cap, to blocks with more rows than the option
+    ``rsvd_rows`` whose cap is below their height; k = min(a, cap + 16)
+    sample columns (oversampling p = 16) of a uniform [-1, 1) test matrix
+    drawn from a counter-based SplitMix64 stream seeded by (level, box, side),
+    q = 1 power iteration, each range basis orthonormalised twice, and the
+    exact SVD of the projected k-row matrix.  Any consumer that uses the same
+    option draws the same test matrix.
 S   symmetric variant (optional; the paper notes that its algorithm is not
     specialised to symmetric matrices and that symmetry could be exploited):
     when A is symmetric and U = V at the leaves, the V-side matrix of every
@@ -69,10 +76,9 @@ LU of E and the solve equals the dense solve of A_n to rounding; the
 two-block example of Appendix C gives the printed closed-form matrix; the
 solve error tracks eps.  The exact rank profile at tau > 0 has no printed
 value to pin against (parity unpinned beyond self-consistency and the error
-bound).  The linear growth of cost and memory in N (Sec. 2.5) is not pinned:
-at the sizes this oracle reaches in seconds (one to three levels) the cost
-is dominated by the first upper level, whose boxes stack eight children's
-ranks, and grows faster than N.
+bound).  The linear growth of cost and memory in N (Sec. 2.5, Sec. 3.1) is
+pinned on counted flops and stored bytes over trees of four to six levels
+(the log-log slope between N and 4N with the leaf occupancy held fixed).
 """
 from __future__ import annotations
 
@@ -129,9 +135,7 @@ def left_svd(M: np.ndarray):
     return W, s
 
 
-SVD_EXACT_MAX_A = 144
-RSVD_ROWS_DEFAULT = 160
-RSVD_OVERSAMPLE = 16
+RSVD_OVERSAMPLE = 16   # oversampling p of the randomised SVD (reading R3b)
 _M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
 
 
@@ -228,7 +232,7 @@ class IFMM:
     """Plain IFMM factorisation of the H^2 matrix A_n defined by ``h2``."""
 
     def __init__(self, h2: H2, eps: float, tau: float | None = None, rank_cap: int | None = None,
-                 sigma0: float | None = None, rsvd_rows: int = RSVD_ROWS_DEFAULT,
+                 sigma0: float | None = None, rsvd_rows: int | None = None,
                  symmetric: bool = False):
         self.h2 = h2
         self.rsvd_rows = rsvd_rows
@@ -388,8 +392,8 @@ class IFMM:
             MV = np.hstack([st.V[j] * st.SV[j][None, :]] + FV)
             aj = st.a[j]
             rcap = self._cap(aj)
-            if self.tau > 0 and aj > self.rsvd_rows and rcap < aj:
-                k = min(aj, rcap + RSVD_OVERSAMPLE, SVD_EXACT_MAX_A)
+            if self.rsvd_rows is not None and self.tau > 0 and aj > self.rsvd_rows and rcap < aj:
+                k = min(aj, rcap + RSVD_OVERSAMPLE)
                 WU, sU = rsvd_left(MU, k, rsvd_seed(st.l, j, 0))
                 WV, sV = (WU, sU) if self.symmetric else rsvd_left(MV, k, rsvd_seed(st.l, j, 1))
                 full = k

@@ -42,3 +42,35 @@ def test_max_iterations_reported():
     b = rng.standard_normal(100)
     x, it, res = gmres(lambda v: A @ v, b, tol=1e-14, maxit=7)
     assert it == 7 and res > 1e-14
+
+
+def test_left_preconditioner_exact_inverse_converges_in_one():
+    """Appendix B: with P^-1 = A^-1 on the left, P^-1 A = I and the first
+    Krylov vector already holds the solution."""
+    rng = np.random.default_rng(4)
+    A = rng.standard_normal((80, 80)) + 10 * np.eye(80)
+    Ai = np.linalg.inv(A)
+    b = rng.standard_normal(80)
+    x, it, res = gmres(lambda v: A @ v, b, precond=lambda v: Ai @ v, tol=1e-10, side="left")
+    assert it == 1
+    assert np.allclose(A @ x, b, atol=1e-9)
+
+
+def test_left_residual_is_the_preconditioned_residual():
+    """Appendix B: the left-preconditioned estimate measures
+    ||P^-1 (b - A x)|| / ||P^-1 b||, not the true residual; a diagonal P that
+    scales rows by 10^[0, 4] makes the two differ, and GMRES on the
+    preconditioned system matches the dense solve of P^-1 A x = P^-1 b."""
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((120, 120)) + 30 * np.eye(120)
+    d = 10.0 ** rng.uniform(0, 4, 120)
+    b = rng.standard_normal(120)
+    Pinv = lambda v: v / d
+    x, it, res = gmres(lambda v: A @ v, b, precond=Pinv, tol=1e-12, side="left")
+    pres = np.linalg.norm(Pinv(b - A @ x)) / np.linalg.norm(Pinv(b))
+    assert abs(res - pres) < 1e-10
+    assert np.allclose(x, np.linalg.solve(A, b), rtol=1e-8)
+    # right preconditioning builds another Krylov space; at this tolerance both
+    # reach the dense solution
+    xr, itr, _ = gmres(lambda v: A @ v, b, precond=Pinv, tol=1e-12, side="right")
+    assert np.allclose(xr, x, rtol=1e-8)
