@@ -93,9 +93,30 @@ typedef struct {
 
 typedef enum { IFMM_MV_FMM = 0, IFMM_MV_DIRECT = 1 } ifmm_matvec_mode;
 
+/* Side of the IFMM preconditioner in GMRES (Sec. 3.2 right, Appendix B left). */
+typedef enum {
+  IFMM_GMRES_RIGHT = 0,    /* A M^-1 u = b, x = M^-1 u; tol on ||b - A x|| / ||b||       */
+  IFMM_GMRES_LEFT = 1,     /* M^-1 A x = M^-1 b; tol on ||M^-1 (b - A x)|| / ||M^-1 b||  */
+  IFMM_GMRES_FLEXIBLE = 2  /* right, keeping z_k = M^-1 v_k and forming x = Z y: exact
+                              for a preconditioner that is not one fixed linear map
+                              (applied in reduced precision); twice the basis memory  */
+} ifmm_gmres_side;
+
+typedef struct {
+  int side;   /* ifmm_gmres_side                                                   */
+  int refine; /* right / flexible: when the recomputed true residual is above tol
+                 although the Arnoldi estimate met it, restart from x at most this
+                 many times (iterations count against the same maxit); >= 0     */
+  int precond_precision; /* IFMM_P_FP64 (0): substitution sweeps in FP64;
+                 IFMM_P_FP32: FP32 sweeps (FP32 copies of the factors, made on
+                 first use), valid only with IFMM_GMRES_FLEXIBLE; products,
+                 orthogonalisation and residuals stay FP64                      */
+} ifmm_gmres_options;
+
 typedef struct {
   int iters;                /* Arnoldi steps taken                                   */
-  double rel_residual;      /* GMRES estimate |g_{k+1}| / ||b||                       */
+  double rel_residual;      /* GMRES estimate |g_{k+1}| / ||b|| (left: of the
+                               preconditioned residual, / ||M^-1 b||)                */
   double true_rel_residual; /* ||b - A x|| / ||b|| recomputed with the same matvec    */
   int status;               /* IFMM_OK or IFMM_ERR_NOT_CONVERGED                      */
 } ifmm_gmres_report;
@@ -186,6 +207,15 @@ ifmm_status ifmm_factor_footprint(const ifmm_factorization* fac, unsigned long l
 ifmm_status ifmm_solve(ifmm_ctx* ctx, const ifmm_factorization* fac, const double* b, double* x,
                        int nrhs, long long ld, ifmm_stream stream);
 
+/* Same as ifmm_solve with the substitution sweeps in precision `prec`:
+ * IFMM_P_FP64 (= ifmm_solve) or IFMM_P_FP32 (FP32 copies of the factors and
+ * of the top system's inverse, built on the first FP32 call -- that call
+ * allocates and synchronises `stream`; b and x stay FP64).  Other precisions
+ * are IFMM_ERR_INVALID_ARG. */
+ifmm_status ifmm_solve_prec(ifmm_ctx* ctx, const ifmm_factorization* fac, int prec,
+                            const double* b, double* x, int nrhs, long long ld,
+                            ifmm_stream stream);
+
 /* ---- matvec (Sec. 3.2) ------------------------------------------------------- */
 /* y = A_n x (IFMM_MV_FMM, Chebyshev order opt->fmm_n) or y = A x
  * (IFMM_MV_DIRECT, O(N^2)).  x, y: device, N x nrhs, ld >= N, must not alias. */
@@ -199,9 +229,10 @@ ifmm_status fmm_matvec(ifmm_ctx* ctx, const ifmm_system* sys, int mode, const do
  * stall on the allocator).
  * Computes the same y = A_n x as fmm_matvec(IFMM_MV_FMM) (the direct product
  * when the system has no tree) but calls no cudaMalloc, cudaFree or other
- * allocating routine: its scratch -- the tree lists it needs and the
- * multipole / local coefficients -- lives in one file-scope device array of
- * 64 MiB that every GPU loading the library holds until the process exits.
+ * allocating routine: its scratch -- the multipole / local coefficients and
+ * x, y in tree order -- lives in one file-scope device array of 64 MiB that
+ * every GPU loading the library holds until the process exits (the tree lists
+ * it walks were copied to the device when the system was created).
  * A system and nrhs whose scratch exceeds 64 MiB are rejected with
  * IFMM_ERR_INVALID_ARG and a message naming the bytes needed.
  * The first call on a device looks up the array's address (device current);
@@ -212,14 +243,28 @@ ifmm_status fmm_matvec_static(ifmm_ctx* ctx, const ifmm_system* sys, const doubl
                               int nrhs, long long ld, ifmm_stream stream);
 
 /* ---- GMRES (Sec. 3.2) -------------------------------------------------------- */
-/* Non-restarted GMRES, x_0 = 0, CGS2 Arnoldi, Givens rotations, the
- * factorisation as right preconditioner (fac may be NULL: unpreconditioned).
- * Each of the nrhs columns is an independent solve.  rep: host array of nrhs
- * reports.  Synchronises `stream` (reads the residual estimate every step).
- * Returns IFMM_ERR_NOT_CONVERGED if any column stopped at maxit above tol. */
+/* GMRES, x_0 = 0, CGS2 Arnoldi, Givens rotations, the factorisation as right
+ * preconditioner (fac may be NULL: unpreconditioned).  Each of the nrhs
+ * columns is an independent solve.  A column stops when the Arnoldi residual
+ * estimate is <= tol ||b||; the true residual ||b - A x|| is then recomputed
+ * with the same matvec, and if rounding left it above tol ||b|| GMRES
+ * restarts from x (at most twice, within the same maxit).  rep: host array of
+ * nrhs reports.  Synchronises `stream` (reads the residual estimate every
+ * step).  Returns IFMM_ERR_NOT_CONVERGED if any column ends above tol. */
 ifmm_status gmres_solve(ifmm_ctx* ctx, const ifmm_system* sys, const ifmm_factorization* fac,
                         int mode, const double* b, double* x, int nrhs, long long ld, double tol,
                         int maxit, ifmm_gmres_report* rep, ifmm_stream stream);
+/* GMRES with the preconditioner on either side (Sec. 3.2, Appendix B) or in
+ * flexible form; opt NULL = right preconditioning with refine = 2, which is
+ * what gmres_solve does.  Right / flexible: a column converges when its
+ * recomputed true residual is <= tol.  Left: when the preconditioned residual
+ * estimate is <= tol (the paper's left-preconditioned criterion);
+ * true_rel_residual still reports ||b - A x|| / ||b||.  fac == NULL ignores
+ * the side (plain GMRES).  Synchronises `stream`. */
+ifmm_status gmres_solve_ex(ifmm_ctx* ctx, const ifmm_system* sys, const ifmm_factorization* fac,
+                           int mode, const double* b, double* x, int nrhs, long long ld, double tol,
+                           int maxit, const ifmm_gmres_options* opt, ifmm_gmres_report* rep,
+                           ifmm_stream stream);
 /* Same with b, x in host memory (copied to and from the device inside). */
 ifmm_status gmres_solve_host(ifmm_ctx* ctx, const ifmm_system* sys,
                              const ifmm_factorization* fac, int mode, const double* b_host,
@@ -243,19 +288,29 @@ ifmm_status ifmm_factor_batch(ifmm_ctx* ctx, ifmm_system* const* sys, int count,
 /* A server owns `workers` threads (0 = 4), each with its own stream.  A worker
  * takes the registered system whose oldest queued request has waited longest
  * and that no other worker is serving, gathers all of that system's queued
- * requests (at most 32 columns) into one block of right-hand sides, runs FP64
- * GMRES (FMM matvec, the factorisation as right preconditioner) on the block
- * -- every column converges on its own -- and returns each request's columns.
- * Requests that arrive while their system is busy join its next block; other
- * systems are served at the same time by the other workers.  Destroy a server
- * only after every ifmm_server_wait has returned. */
+ * requests (at most 32 columns) into one block of right-hand sides, runs GMRES
+ * (FMM matvec, the factorisation as preconditioner, true residual <= tol in
+ * FP64) on the block -- every column converges on its own -- and returns each
+ * request's columns.  Requests that arrive while their system is busy join its
+ * next block; other systems are served at the same time by the other workers.
+ * Device memory is admitted against hbm_budget twice: a system's resident
+ * data at ifmm_server_register, and each block's GMRES memory when the block
+ * starts (a block that does not fit waits for running blocks to finish; one
+ * that can never fit completes with IFMM_ERR_BUDGET).  ifmm_server_create
+ * sweeps the preconditioner in FP32 (flexible GMRES); ifmm_server_create_ex
+ * takes precond_precision IFMM_P_FP64 (right-preconditioned GMRES, FP64
+ * sweeps) or IFMM_P_FP32.  Destroy a server only after every ifmm_server_wait
+ * has returned. */
 ifmm_status ifmm_server_create(ifmm_ctx* ctx, unsigned long long hbm_budget, int workers,
                                ifmm_server** out);
+ifmm_status ifmm_server_create_ex(ifmm_ctx* ctx, unsigned long long hbm_budget, int workers,
+                                  int precond_precision, ifmm_server** out);
 void ifmm_server_destroy(ifmm_server* srv);
-/* Admits (sys, fac) if its device memory -- operators, factorisation, solve
- * plans and the GMRES workspace of one 32-column block with maxit iterations
- * -- fits what is left of hbm_budget; IFMM_ERR_BUDGET otherwise (nothing is
- * registered).  A system or factorisation registered twice is
+/* Admits (sys, fac) if its resident device memory -- operators,
+ * factorisation, solve plans and (FP32 server) the FP32 copies of the
+ * factors, which this call builds -- fits what is left of hbm_budget;
+ * IFMM_ERR_BUDGET otherwise (nothing is registered).  maxit: the largest
+ * maxit its requests will use.  A system or factorisation registered twice is
  * IFMM_ERR_INVALID_ARG.  The server does not own sys or fac; they must outlive it.
  * *id: the handle for ifmm_server_submit. */
 ifmm_status ifmm_server_register(ifmm_server* srv, ifmm_system* sys, ifmm_factorization* fac,
@@ -269,6 +324,10 @@ ifmm_status ifmm_server_register(ifmm_server* srv, ifmm_system* sys, ifmm_factor
  * the queueing delay to about one block's solve time. */
 ifmm_status ifmm_server_submit(ifmm_server* srv, int id, const double* b_host, double* x_host,
                                int nrhs, double tol, int maxit, long long* ticket);
+/* Same as ifmm_server_submit with b and x in device memory of the context's
+ * device (N x nrhs, ld N); both must stay valid until the ticket is waited for. */
+ifmm_status ifmm_server_submit_device(ifmm_server* srv, int id, const double* b, double* x,
+                                      int nrhs, double tol, int maxit, long long* ticket);
 /* Waits up to timeout_ms (< 0: no limit) for a ticket; IFMM_ERR_TIMEOUT if it
  * is not done yet (the ticket stays valid).  On completion fills rep (nrhs
  * entries, host), *latency_s (submit to completion, seconds; may be NULL),
@@ -301,6 +360,15 @@ ifmm_status ifmm_profile_start(ifmm_ctx* ctx);
 /* Synchronise the device, stop recording and return per-kernel totals in
  * stats (host array of `capacity`); *count receives the number of kernels. */
 ifmm_status ifmm_profile_stop(ifmm_ctx* ctx, ifmm_kernel_stat* stats, int capacity, int* count);
+
+/* Kernel launches the library has made in this process so far (graph replays
+ * count every kernel node of the graph). */
+ifmm_status ifmm_launch_count(unsigned long long* launches);
+
+/* Measured peak arithmetic rates of the context's device (TFLOP/s): FP64 and
+ * FP32 FMA chains over every SM, timed with CUDA events (~0.1 s).  The
+ * roofline denominators of the library's FP64- and FP32-bound kernels. */
+ifmm_status ifmm_measure_peaks(ifmm_ctx* ctx, double* fp64_tflops, double* fp32_tflops);
 
 #ifdef __cplusplus
 }

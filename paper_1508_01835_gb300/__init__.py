@@ -25,6 +25,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error",
 K_INV_R, K_GAUSSIAN, K_PAPER_D = 0, 1, 2
 P_FP64, P_TF32, P_BF16, P_FP32 = 0, 1, 2, 3
 MV_FMM, MV_DIRECT = 0, 1
+GMRES_RIGHT, GMRES_LEFT, GMRES_FLEXIBLE = 0, 1, 2
 
 
 class Kernel(C.Structure):
@@ -40,6 +41,10 @@ class Options(C.Structure):
 class GmresReport(C.Structure):
     _fields_ = [("iters", C.c_int), ("rel_residual", C.c_double),
                 ("true_rel_residual", C.c_double), ("status", C.c_int)]
+
+
+class GmresOptions(C.Structure):
+    _fields_ = [("side", C.c_int), ("refine", C.c_int), ("precond_precision", C.c_int)]
 
 
 class SystemInfo(C.Structure):
@@ -103,14 +108,21 @@ def lib() -> C.CDLL:
         "ifmm_factor_get_ranks": (C.c_int, [P, C.c_int, P, C.c_int, C.POINTER(C.c_int)]),
         "ifmm_factor_footprint": (C.c_int, [P, C.POINTER(C.c_ulonglong)]),
         "ifmm_solve": (C.c_int, [P, P, P, P, C.c_int, C.c_longlong, P]),
+        "ifmm_solve_prec": (C.c_int, [P, P, C.c_int, P, P, C.c_int, C.c_longlong, P]),
         "fmm_matvec": (C.c_int, [P, P, C.c_int, P, P, C.c_int, C.c_longlong, P]),
         "gmres_solve": (C.c_int, [P, P, P, C.c_int, P, P, C.c_int, C.c_longlong, C.c_double,
                                   C.c_int, C.POINTER(GmresReport), P]),
+        "gmres_solve_ex": (C.c_int, [P, P, P, C.c_int, P, P, C.c_int, C.c_longlong, C.c_double,
+                                     C.c_int, C.POINTER(GmresOptions), C.POINTER(GmresReport),
+                                     P]),
         "gmres_solve_host": (C.c_int, [P, P, P, C.c_int, P, P, C.c_int, C.c_longlong,
                                        C.c_double, C.c_int, C.POINTER(GmresReport), P]),
         "fmm_matvec_static": (C.c_int, [P, P, P, P, C.c_int, C.c_longlong, P]),
         "ifmm_factor_batch": (C.c_int, [P, P, C.c_int, P, P]),
         "ifmm_server_create": (C.c_int, [P, C.c_ulonglong, C.c_int, C.POINTER(P)]),
+        "ifmm_server_create_ex": (C.c_int, [P, C.c_ulonglong, C.c_int, C.c_int, C.POINTER(P)]),
+        "ifmm_server_submit_device": (C.c_int, [P, C.c_int, P, P, C.c_int, C.c_double, C.c_int,
+                                                C.POINTER(C.c_longlong)]),
         "ifmm_server_destroy": (None, [P]),
         "ifmm_server_register": (C.c_int, [P, P, P, C.c_int, C.POINTER(C.c_int)]),
         "ifmm_server_submit": (C.c_int, [P, C.c_int, P, P, C.c_int, C.c_double, C.c_int,
@@ -123,6 +135,8 @@ def lib() -> C.CDLL:
         "ifmm_schur_product": (C.c_int, [P, C.c_int, C.c_int, C.c_int, C.c_int, P, C.c_int,
                                          C.c_int, P, C.c_int, C.c_int, P, C.c_int, C.c_double,
                                          C.c_double, P]),
+        "ifmm_measure_peaks": (C.c_int, [P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+        "ifmm_launch_count": (C.c_int, [C.POINTER(C.c_ulonglong)]),
         "ifmm_profile_start": (C.c_int, [P]),
         "ifmm_profile_stop": (C.c_int, [P, C.POINTER(KernelStat), C.c_int, C.POINTER(C.c_int)]),
     }
@@ -261,6 +275,13 @@ def ifmm_solve(ctx, fac, b, x, N: int, stream=None):
     _check(lib().ifmm_solve(ctx, fac, pb, px, k, ld, _stream(stream)), ctx)
 
 
+def ifmm_solve_prec(ctx, fac, prec: int, b, x, N: int, stream=None):
+    pb, k, ld = _vec(b, N)
+    px, k2, _ = _vec(x, N)
+    assert k == k2
+    _check(lib().ifmm_solve_prec(ctx, fac, prec, pb, px, k, ld, _stream(stream)), ctx)
+
+
 def fmm_matvec(ctx, sys, mode: int, x, y, N: int, stream=None):
     px, k, ld = _vec(x, N)
     py, k2, _ = _vec(y, N)
@@ -283,6 +304,18 @@ def gmres_solve(ctx, sys, fac, mode: int, b, x, N: int, tol=1e-10, maxit=500, st
     reps = (GmresReport * k)()
     _check(lib().gmres_solve(ctx, sys, fac, mode, pb, px, k, ld, tol, maxit, reps,
                              _stream(stream)), ctx, allow=(5,))
+    return list(reps)
+
+
+def gmres_solve_ex(ctx, sys, fac, mode: int, b, x, N: int, tol=1e-10, maxit=500,
+                   side=GMRES_RIGHT, refine=2, precond_precision=P_FP64, stream=None):
+    pb, k, ld = _vec(b, N)
+    px, k2, _ = _vec(x, N)
+    assert k == k2
+    reps = (GmresReport * k)()
+    o = GmresOptions(side, refine, precond_precision)
+    _check(lib().gmres_solve_ex(ctx, sys, fac, mode, pb, px, k, ld, tol, maxit, C.byref(o), reps,
+                                _stream(stream)), ctx, allow=(5,))
     return list(reps)
 
 
@@ -320,9 +353,13 @@ def _scheck(st, srv, allow=()):
     return st
 
 
-def ifmm_server_create(ctx, hbm_budget: int, workers: int = 0):
+def ifmm_server_create(ctx, hbm_budget: int, workers: int = 0, precond_precision=None):
     h = P()
-    _check(lib().ifmm_server_create(ctx, hbm_budget, workers, C.byref(h)), ctx)
+    if precond_precision is None:
+        _check(lib().ifmm_server_create(ctx, hbm_budget, workers, C.byref(h)), ctx)
+    else:
+        _check(lib().ifmm_server_create_ex(ctx, hbm_budget, workers, precond_precision,
+                                           C.byref(h)), ctx)
     return h
 
 
@@ -346,6 +383,17 @@ def ifmm_server_submit(srv, sid: int, b_np, x_np, tol=1e-10, maxit=100) -> int:
     t = C.c_longlong()
     _scheck(lib().ifmm_server_submit(srv, sid, b_np.ctypes.data_as(P), x_np.ctypes.data_as(P), k,
                                      tol, maxit, C.byref(t)), srv)
+    return t.value
+
+
+def ifmm_server_submit_device(srv, sid: int, b, x, N: int, tol=1e-10, maxit=100) -> int:
+    """b, x: float64 CUDA tensors (nrhs, N) or (N,); both must stay alive until
+    the ticket is waited for."""
+    pb, k, _ = _vec(b, N)
+    px, k2, _ = _vec(x, N)
+    assert k == k2
+    t = C.c_longlong()
+    _scheck(lib().ifmm_server_submit_device(srv, sid, pb, px, k, tol, maxit, C.byref(t)), srv)
     return t.value
 
 
@@ -377,6 +425,20 @@ def ifmm_schur_product(ctx, prec: int, M: int, N: int, K: int, A, lda: int, tran
     _check(lib().ifmm_schur_product(ctx, prec, M, N, K, P(A.data_ptr()), lda, transA,
                                     P(B.data_ptr()), ldb, transB, P(Cm.data_ptr()), ldc,
                                     alpha, beta, _stream(stream)), ctx)
+
+
+def ifmm_measure_peaks(ctx):
+    """(FP64, FP32) TFLOP/s measured on the context's device."""
+    a, b = C.c_double(), C.c_double()
+    _check(lib().ifmm_measure_peaks(ctx, C.byref(a), C.byref(b)), ctx)
+    return a.value, b.value
+
+
+def ifmm_launch_count() -> int:
+    """Kernel launches the library has made in this process so far."""
+    n = C.c_ulonglong()
+    _check(lib().ifmm_launch_count(C.byref(n)))
+    return n.value
 
 
 def ifmm_profile_start(ctx):

@@ -173,6 +173,19 @@ ifmm_status ifmm_solve(ifmm_ctx* ctx, const ifmm_factorization* fac, const doubl
   });
 }
 
+ifmm_status ifmm_solve_prec(ifmm_ctx* ctx, const ifmm_factorization* fac, int prec,
+                            const double* b, double* x, int nrhs, long long ld,
+                            ifmm_stream stream) {
+  if (!ctx || !fac || !b || !x || nrhs < 0) return IFMM_ERR_INVALID_ARG;
+  if (ld < fac->sys->N || (prec != IFMM_P_FP64 && prec != IFMM_P_FP32)) return IFMM_ERR_INVALID_ARG;
+  return guard(ctx, [&] {
+    CK(cudaSetDevice(ctx->device));
+    auto* f = const_cast<ifmm_factorization*>(fac);
+    if (prec == IFMM_P_FP32) factor_solve_f32(f, b, ld, x, ld, nrhs, st(stream));
+    else factor_solve(f, b, ld, x, ld, nrhs, st(stream));
+  });
+}
+
 ifmm_status fmm_matvec(ifmm_ctx* ctx, const ifmm_system* sys, int mode, const double* x,
                        double* y, int nrhs, long long ld, ifmm_stream stream) {
   if (!ctx || !sys || !x || !y || nrhs < 0) return IFMM_ERR_INVALID_ARG;
@@ -206,6 +219,35 @@ ifmm_status gmres_solve(ifmm_ctx* ctx, const ifmm_system* sys, const ifmm_factor
     CK(cudaSetDevice(ctx->device));
     res = gmres_run(const_cast<ifmm_system*>(sys), const_cast<ifmm_factorization*>(fac), mode, b,
                     x, nrhs, ld, tol, maxit, rep, st(stream));
+  });
+  return g != IFMM_OK ? g : res;
+}
+
+ifmm_status gmres_solve_ex(ifmm_ctx* ctx, const ifmm_system* sys, const ifmm_factorization* fac,
+                           int mode, const double* b, double* x, int nrhs, long long ld, double tol,
+                           int maxit, const ifmm_gmres_options* opt, ifmm_gmres_report* rep,
+                           ifmm_stream stream) {
+  if (!ctx || !sys || !b || !x || !rep || nrhs < 1) return IFMM_ERR_INVALID_ARG;
+  if (ld < sys->N || maxit < 1 || !(tol > 0.0)) return IFMM_ERR_INVALID_ARG;
+  if (mode != IFMM_MV_FMM && mode != IFMM_MV_DIRECT) return IFMM_ERR_INVALID_ARG;
+  if (fac && fac->sys != sys) return IFMM_ERR_INVALID_ARG;
+  GmresOpts go;
+  if (opt) {
+    if (opt->side < IFMM_GMRES_RIGHT || opt->side > IFMM_GMRES_FLEXIBLE || opt->refine < 0)
+      return IFMM_ERR_INVALID_ARG;
+    if (opt->precond_precision != IFMM_P_FP64 && opt->precond_precision != IFMM_P_FP32)
+      return IFMM_ERR_INVALID_ARG;
+    if (opt->precond_precision == IFMM_P_FP32 && fac && opt->side != IFMM_GMRES_FLEXIBLE)
+      return IFMM_ERR_INVALID_ARG;
+    go.side = opt->side;
+    go.refine = opt->refine;
+    go.precond_fp32 = opt->precond_precision == IFMM_P_FP32;
+  }
+  ifmm_status res = IFMM_OK;
+  ifmm_status g = guard(ctx, [&] {
+    CK(cudaSetDevice(ctx->device));
+    res = gmres_run(const_cast<ifmm_system*>(sys), const_cast<ifmm_factorization*>(fac), mode, b,
+                    x, nrhs, ld, tol, maxit, rep, st(stream), nullptr, go);
   });
   return g != IFMM_OK ? g : res;
 }

@@ -9,16 +9,20 @@
 // factor.cu); the launches of different systems run concurrently on the GPU,
 // filling the SMs that one system's small colour classes leave idle.
 //
-// Server: requests (one system, nrhs right-hand sides in host memory, a
-// tolerance) are queued per registered system.  Worker threads, each with its
-// own stream, repeatedly take the system whose oldest request has waited
-// longest and that no other worker is serving, gather ALL of that system's
-// queued requests (up to a column cap) into one block of right-hand sides and
-// run FP64 GMRES on the block (each column converges independently, Sec. 3.2),
-// then return every request's columns.  Requests that arrive while their
-// system is busy join its next block; other systems proceed in parallel on
-// the other workers.  Registration admits a system only if the device memory
-// of its factorisation, operators and GMRES workspace fits the budget.
+// Server: requests (one system, nrhs right-hand sides in host or device
+// memory, a tolerance) are queued per registered system.  Worker threads,
+// each with its own stream, repeatedly take the system whose oldest request
+// has waited longest and that no other worker is serving, gather ALL of that
+// system's queued requests (up to a column cap) into one block of right-hand
+// sides and run GMRES on the block (each column converges independently,
+// Sec. 3.2) -- by default flexible GMRES with the substitution sweeps in FP32
+// and products, orthogonalisation and residuals in FP64 -- then return every
+// request's columns.  Requests that arrive while their system is busy join
+// its next block; other systems proceed in parallel on the other workers.
+// Device memory is admitted twice against the budget: a system's resident
+// data (operators, factorisation, FP32 copies, plans) at registration, and
+// each block's GMRES memory when the block starts; a block that does not fit
+// waits until running blocks finish (idle workers hand back their memory).
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -96,8 +100,9 @@ ifmm_status factor_batch(int device, ifmm_system* const* sys, int count, cudaStr
 struct ifmm_server {
   struct Request {
     int id = 0, nrhs = 0;
-    const double* b = nullptr;  // host, N x nrhs, ld N
-    double* x = nullptr;        // host, N x nrhs, ld N
+    const double* b = nullptr;  // N x nrhs, ld N: host, or device when `device`
+    double* x = nullptr;
+    bool device = false;
     double tol = 1e-10;
     int maxit = 500;
     ifmm::SteadyClock::time_point t_submit, t_done;
@@ -114,21 +119,57 @@ struct ifmm_server {
   };
   ifmm_ctx* ctx = nullptr;
   int device = 0;
-  size_t budget = 0, used = 0;
+  int precond_fp32 = 1;  // flexible GMRES with FP32 substitution sweeps
+  size_t budget = 0, used = 0;  // used: resident systems (operators, factors, plans)
   int col_cap = 32;
   int queue_cap = 32;  // queued columns per system (one block) beyond which requests are shed
-  long long shed = 0;
+  long long shed = 0, refused = 0;
   std::deque<Entry> systems;  // stable references while workers hold one
   std::map<long long, std::unique_ptr<Request>> reqs;
   long long next_ticket = 1;
   long long batches = 0, batched_columns = 0;
+  // GMRES working memory of the blocks: reserved per worker (what its arena
+  // holds, or what its running block may grow it to), admitted block by block
+  std::vector<size_t> ws_res;
+  size_t ws_total = 0;
+  int running = 0, mem_waiters = 0;
+  bool release_req = false;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   bool stop = false;
   std::vector<std::thread> workers;
   std::string last_error;
 
-  void work() {
+  // device bytes a block of `width` columns may use: Krylov basis (and the
+  // preconditioned basis of flexible GMRES) of maxit + 1 vectors in chunks of
+  // 16, four work vectors, the block's b and x
+  size_t block_bytes(long long N, int width, int maxit) const {
+    const long long vecs = ((maxit + 16) / 16) * 16;
+    const long long nb = precond_fp32 ? 2 : 1;
+    return sizeof(double) * (size_t)N * width * (size_t)(nb * vecs + 6);
+  }
+
+  void finish(std::vector<Request*>& batch, ifmm_status st, const std::string& msg,
+              const std::vector<ifmm_gmres_report>& reps, int cols) {
+    // caller holds the lock
+    const auto now = ifmm::SteadyClock::now();
+    long long off = 0;
+    for (Request* r : batch) {
+      r->rep.assign(reps.begin() + off, reps.begin() + off + r->nrhs);
+      off += r->nrhs;
+      r->status = st;
+      if (st == IFMM_OK)
+        for (auto& q : r->rep)
+          if (q.status != IFMM_OK) r->status = (ifmm_status)q.status;
+      r->t_done = now;
+      r->done = true;
+    }
+    if (!msg.empty()) last_error = msg;
+    batches++;
+    batched_columns += cols;
+  }
+
+  void work(int w) {
     using namespace ifmm;
     cudaStream_t ws = nullptr;
     Arena buf;
@@ -145,8 +186,20 @@ struct ifmm_server {
       last_error = e.what();
       return;
     }
+    auto held = [&] { return gws.held + buf.held; };
     std::unique_lock<std::mutex> lk(mu);
     while (!stop) {
+      if (release_req && held() > 0) {  // another block waits for memory this idle worker holds
+        lk.unlock();
+        gws.release();
+        buf.release();
+        buf_cols = 0;
+        buf_n = 0;
+        lk.lock();
+        ws_total -= ws_res[w];
+        ws_res[w] = 0;
+        cv_done.notify_all();
+      }
       // the idle system whose oldest request has waited longest
       int pick = -1;
       SteadyClock::time_point best{};
@@ -163,20 +216,56 @@ struct ifmm_server {
       Entry& E = systems[pick];
       E.busy = true;
       std::vector<Request*> batch;
-      int cols = 0;
+      int cols = 0, maxit = 1;
+      double tol = 1.0;
       while (!E.queue.empty()) {
         Request* r = reqs[E.queue.front()].get();
         if (!batch.empty() && cols + r->nrhs > col_cap) break;
         batch.push_back(r);
         cols += r->nrhs;
+        tol = std::min(tol, r->tol);
+        maxit = std::max(maxit, r->maxit);
         E.queue.pop_front();
       }
-      lk.unlock();
       // pad to a power of two so that the solve and matvec plans of a few
       // widths are reused; padding columns are zero and never iterate
       int width = 1;
       while (width < cols) width <<= 1;
       const long long N = E.sys->N;
+      // admission of the block's working memory: wait while running blocks
+      // (or idle workers' arenas) hold what it needs
+      const size_t need = std::max(block_bytes(N, width, maxit), held());
+      bool fits = false;
+      for (;;) {
+        if (used + ws_total - ws_res[w] + need <= budget) { fits = true; break; }
+        bool idle_memory = false;
+        for (int v = 0; v < (int)ws_res.size(); v++) idle_memory |= v != w && ws_res[v] > 0;
+        if (running == 0 && !idle_memory) break;  // can never fit
+        release_req = idle_memory;
+        mem_waiters++;
+        cv_work.notify_all();
+        cv_done.wait(lk);
+        mem_waiters--;
+        if (mem_waiters == 0) release_req = false;
+        if (stop) break;
+      }
+      if (!fits) {
+        refused += (long long)batch.size();
+        std::vector<ifmm_gmres_report> none(cols);
+        for (auto& q : none) q = {0, 0.0, 0.0, IFMM_ERR_BUDGET};
+        finish(batch, IFMM_ERR_BUDGET,
+               "a block of " + std::to_string(width) + " columns needs " + std::to_string(need) +
+                   " bytes of GMRES memory beyond what the budget leaves",
+               none, cols);
+        E.busy = false;
+        cv_done.notify_all();
+        cv_work.notify_all();
+        continue;
+      }
+      ws_total += need - ws_res[w];
+      ws_res[w] = need;
+      running++;
+      lk.unlock();
       ifmm_status st = IFMM_OK;
       std::string msg;
       std::vector<ifmm_gmres_report> reps(width);
@@ -189,21 +278,23 @@ struct ifmm_server {
           dx = buf.alloc<double>((size_t)buf_n * buf_cols);
         }
         CK(cudaMemsetAsync(db, 0, sizeof(double) * N * width, ws));
-        double tol = 1.0;
-        int maxit = 1;
         long long off = 0;
         for (Request* r : batch) {
           CK(cudaMemcpyAsync(db + off * N, r->b, sizeof(double) * N * r->nrhs,
-                             cudaMemcpyHostToDevice, ws));
+                             r->device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ws));
           off += r->nrhs;
-          tol = std::min(tol, r->tol);
-          maxit = std::max(maxit, r->maxit);
         }
-        gmres_run(E.sys, E.fac, IFMM_MV_FMM, db, dx, width, N, tol, maxit, reps.data(), ws, &gws);
+        GmresOpts go;
+        if (precond_fp32) {
+          go.side = IFMM_GMRES_FLEXIBLE;
+          go.precond_fp32 = 1;
+        }
+        gmres_run(E.sys, E.fac, IFMM_MV_FMM, db, dx, width, N, tol, maxit, reps.data(), ws, &gws,
+                  go);
         off = 0;
         for (Request* r : batch) {
           CK(cudaMemcpyAsync(r->x, dx + off * N, sizeof(double) * N * r->nrhs,
-                             cudaMemcpyDeviceToHost, ws));
+                             r->device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ws));
           off += r->nrhs;
         }
         CK(cudaStreamSynchronize(ws));
@@ -214,22 +305,13 @@ struct ifmm_server {
         st = IFMM_ERR_CUDA;
         msg = e.what();
       }
-      const auto now = SteadyClock::now();
       lk.lock();
-      long long off = 0;
-      for (Request* r : batch) {
-        r->rep.assign(reps.begin() + off, reps.begin() + off + r->nrhs);
-        off += r->nrhs;
-        r->status = st;
-        if (st == IFMM_OK)
-          for (auto& q : r->rep)
-            if (q.status != IFMM_OK) r->status = (ifmm_status)q.status;
-        r->t_done = now;
-        r->done = true;
-      }
-      if (!msg.empty()) last_error = msg;
-      batches++;
-      batched_columns += cols;
+      running--;
+      const size_t h = held();  // what the arena keeps after the block
+      ws_total -= ws_res[w];
+      ws_res[w] = h;
+      ws_total += h;
+      finish(batch, st, msg, reps, cols);
       E.busy = false;
       cv_done.notify_all();
       cv_work.notify_all();
@@ -272,17 +354,26 @@ ifmm_status ifmm_factor_batch(ifmm_ctx* ctx, ifmm_system* const* sys, int count,
   return st;
 }
 
-ifmm_status ifmm_server_create(ifmm_ctx* ctx, unsigned long long hbm_budget, int workers,
-                               ifmm_server** out) {
+ifmm_status ifmm_server_create_ex(ifmm_ctx* ctx, unsigned long long hbm_budget, int workers,
+                                  int precond_precision, ifmm_server** out) {
   if (!ctx || !out || workers < 0 || workers > 64) return IFMM_ERR_INVALID_ARG;
+  if (precond_precision != IFMM_P_FP64 && precond_precision != IFMM_P_FP32)
+    return IFMM_ERR_INVALID_ARG;
   auto* s = new ifmm_server();
   s->ctx = ctx;
   s->device = ctx->device;
   s->budget = hbm_budget;
+  s->precond_fp32 = precond_precision == IFMM_P_FP32;
   const int nw = workers > 0 ? workers : 4;
-  for (int w = 0; w < nw; w++) s->workers.emplace_back([s] { s->work(); });
+  s->ws_res.assign(nw, 0);
+  for (int w = 0; w < nw; w++) s->workers.emplace_back([s, w] { s->work(w); });
   *out = s;
   return IFMM_OK;
+}
+
+ifmm_status ifmm_server_create(ifmm_ctx* ctx, unsigned long long hbm_budget, int workers,
+                               ifmm_server** out) {
+  return ifmm_server_create_ex(ctx, hbm_budget, workers, IFMM_P_FP32, out);
 }
 
 void ifmm_server_destroy(ifmm_server* s) {
@@ -299,22 +390,44 @@ void ifmm_server_destroy(ifmm_server* s) {
 ifmm_status ifmm_server_register(ifmm_server* s, ifmm_system* sys, ifmm_factorization* fac,
                                  int maxit, int* id) {
   if (!s || !sys || !fac || !id || fac->sys != sys || maxit < 1) return IFMM_ERR_INVALID_ARG;
-  // device memory: operators + factorisation + GMRES workspace of one block of
-  // col_cap columns (Krylov basis of maxit + 1 vectors, solve and matvec plans)
-  const size_t cols = (size_t)s->col_cap;
-  const size_t gm = sizeof(double) * (size_t)sys->N * cols * ((size_t)maxit + 8);
-  const size_t bytes = sys->mem.held + fac->store.held + fac->plan_bytes() + gm;
+  {
+    std::lock_guard<std::mutex> g(s->mu);
+    for (const auto& e : s->systems)
+      if (e.sys == sys || e.fac == fac) {  // a system is served by one worker at a time
+        s->last_error = "this system or factorisation is already registered";
+        return IFMM_ERR_INVALID_ARG;
+      }
+  }
+  // resident device memory: operators, factorisation, its FP32 copies (built
+  // here when the server sweeps in FP32) and solve plans; the GMRES memory of
+  // a block is admitted when the block starts
+  size_t bytes = sys->mem.held + fac->store.held + fac->plan_bytes();
+  if (s->precond_fp32 && !fac->f32.ready) {
+    size_t est = 0;
+    for (const auto& R : fac->recs)
+      est += sizeof(float) * ((size_t)R.p * R.a + 2 * (size_t)R.nC * R.a);
+    const long long n = sys->L == 0 ? sys->N : fac->top_n;
+    est += sizeof(float) * (size_t)n * n;
+    bytes += est;
+  }
   std::lock_guard<std::mutex> g(s->mu);
-  for (const auto& e : s->systems)
-    if (e.sys == sys || e.fac == fac) {  // a system is served by one worker at a time
-      s->last_error = "this system or factorisation is already registered";
-      return IFMM_ERR_INVALID_ARG;
-    }
   if (s->used + bytes > s->budget) {
     s->last_error = "admission refused: the system needs " + std::to_string(bytes) +
                     " bytes of device memory, " + std::to_string(s->budget - s->used) +
                     " remain in the budget";
     return IFMM_ERR_BUDGET;
+  }
+  if (s->precond_fp32 && !fac->f32.ready) {
+    try {
+      CK(cudaSetDevice(s->device));
+      cudaStream_t st = nullptr;
+      CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+      ifmm::factor_prepare_f32(fac, st);
+      cudaStreamDestroy(st);
+    } catch (const std::exception& e) {
+      s->last_error = e.what();
+      return IFMM_ERR_CUDA;
+    }
   }
   s->used += bytes;
   ifmm_server::Entry e;
@@ -326,9 +439,9 @@ ifmm_status ifmm_server_register(ifmm_server* s, ifmm_system* sys, ifmm_factoriz
   return IFMM_OK;
 }
 
-ifmm_status ifmm_server_submit(ifmm_server* s, int id, const double* b_host, double* x_host,
-                               int nrhs, double tol, int maxit, long long* ticket) {
-  if (!s || !b_host || !x_host || !ticket || nrhs < 1 || !(tol > 0.0) || maxit < 1)
+static ifmm_status server_submit(ifmm_server* s, int id, const double* b, double* x, bool device,
+                                 int nrhs, double tol, int maxit, long long* ticket) {
+  if (!s || !b || !x || !ticket || nrhs < 1 || !(tol > 0.0) || maxit < 1)
     return IFMM_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> g(s->mu);
   if (id < 0 || id >= (int)s->systems.size()) return IFMM_ERR_INVALID_ARG;
@@ -348,8 +461,9 @@ ifmm_status ifmm_server_submit(ifmm_server* s, int id, const double* b_host, dou
   auto r = std::make_unique<ifmm_server::Request>();
   r->id = id;
   r->nrhs = nrhs;
-  r->b = b_host;
-  r->x = x_host;
+  r->b = b;
+  r->x = x;
+  r->device = device;
   r->tol = tol;
   r->maxit = maxit;
   r->t_submit = ifmm::SteadyClock::now();
@@ -359,6 +473,16 @@ ifmm_status ifmm_server_submit(ifmm_server* s, int id, const double* b_host, dou
   *ticket = t;
   s->cv_work.notify_one();
   return IFMM_OK;
+}
+
+ifmm_status ifmm_server_submit(ifmm_server* s, int id, const double* b_host, double* x_host,
+                               int nrhs, double tol, int maxit, long long* ticket) {
+  return server_submit(s, id, b_host, x_host, false, nrhs, tol, maxit, ticket);
+}
+
+ifmm_status ifmm_server_submit_device(ifmm_server* s, int id, const double* b, double* x,
+                                      int nrhs, double tol, int maxit, long long* ticket) {
+  return server_submit(s, id, b, x, true, nrhs, tol, maxit, ticket);
 }
 
 ifmm_status ifmm_server_wait(ifmm_server* s, long long ticket, int timeout_ms,

@@ -33,7 +33,7 @@ static double since(Clock::time_point t) {
 static bool tracing() {
   static const bool v = [] {
     const char* e = std::getenv("IFMM_TRACE");
-    return e && (e[0] == '1' || e[0] == '2');
+    return e && (e[0] == '1' || e[0] == '2' || e[0] == '3');
   }();
   return v;
 }
@@ -44,6 +44,43 @@ static bool tracing() {
       std::fflush(stderr);              \
     }                                   \
   } while (0)
+
+// IFMM_TRACE=3: after each stage of a colour, copy the blocks it produced to
+// the host and report the first one holding a non-finite value (debugging aid;
+// synchronises and is slow).
+static bool checking() {
+  static const bool v = [] {
+    const char* e = std::getenv("IFMM_TRACE");
+    return e && e[0] == '3';
+  }();
+  return v;
+}
+static void check_finite(const char* stage, int l, const std::vector<int>& boxes,
+                         const std::vector<std::pair<const double*, size_t>>& arrays,
+                         cudaStream_t s) {
+  if (!checking()) return;
+  CK(cudaStreamSynchronize(s));
+  for (size_t k = 0; k < arrays.size(); k++) {
+    if (!arrays[k].first || arrays[k].second == 0) continue;
+    std::vector<double> h(arrays[k].second);
+    CK(cudaMemcpy(h.data(), arrays[k].first, h.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    size_t bad = 0;
+    double mx = 0.0;
+    for (double v : h) {
+      if (!std::isfinite(v)) bad++;
+      else mx = std::max(mx, std::fabs(v));
+    }
+    if (bad) {
+      std::fprintf(stderr, "[ifmm-check] level %d %s: array %zu of %zu has %zu non-finite of %zu (boxes",
+                   l, stage, k, arrays.size(), bad, h.size());
+      for (int b : boxes) std::fprintf(stderr, " %d", b);
+      std::fprintf(stderr, ")\n");
+      return;
+    }
+    if (mx > 1e100)
+      std::fprintf(stderr, "[ifmm-check] level %d %s: array %zu max |v| %.3g\n", l, stage, k, mx);
+  }
+}
 
 static inline GemmTask gm(const double* A, int lda, int tA, const double* B, int ldb, int tB,
                           double* C, int ldc, int M, int N, int K, double alpha, double beta) {
@@ -86,12 +123,10 @@ struct FLevel {
 };
 
 // Blocks taller than rsvd_rows (default 160) are recompressed with the
-// randomised SVD when the rank cap is below the block height and truncation
-// is on (tau > 0): the top k = min(a, cap + oversampling, 144) singular
-// triplets decide the rank.
-static int rsvd_k(int a, int rcap) {
-  return std::min(std::min(a, rcap + RSVD_OVERSAMPLE), SVD_EXACT_MAX_A);
-}
+// randomised SVD of Sec. 2.4 when the rank cap is below the block height and
+// truncation is on (tau > 0): the top k = min(a, cap + 16) singular triplets
+// decide the rank (oversampling 16, one power iteration).
+static int rsvd_k(int a, int rcap) { return std::min(a, rcap + RSVD_OVERSAMPLE); }
 
 struct Factorizer {
   ifmm_system* sys;
@@ -433,7 +468,8 @@ struct Factorizer {
     scratch.reset();
     const int nbx = (int)boxes.size();
     std::vector<FRec> recs(nbx);
-    std::vector<double*> S(nbx);
+    std::vector<double*> S(nbx), LU(nbx), ERP(nbx), G(nbx);
+    std::vector<int*> piv(nbx);
     std::vector<CopyTask> cps;
     std::vector<LuTask> lus;
     std::vector<RsTask> rss;
@@ -460,40 +496,76 @@ struct Factorizer {
       off += R.r;
       R.nC = off;
       const int p = R.p, nC = R.nC, a = R.a, r = R.r;
-      R.LU = f->store.alloc<double>((size_t)p * p);
-      R.piv = f->store.alloc<int>(p);
+      LU[b] = scratch.alloc<double>((size_t)p * p);
+      piv[b] = scratch.alloc<int>(p);
       R.info = f->store.alloc<int>(1);
-      R.ERP = f->store.alloc<double>((size_t)nC * p);
-      R.G = f->store.alloc<double>((size_t)p * nC);
-      CK(cudaMemsetAsync(R.ERP, 0, sizeof(double) * (size_t)nC * p, s));
-      CK(cudaMemsetAsync(R.G, 0, sizeof(double) * (size_t)p * nC, s));
+      ERP[b] = scratch.alloc<double>((size_t)nC * p);
+      G[b] = scratch.alloc<double>((size_t)p * nC);
+      CK(cudaMemsetAsync(ERP[b], 0, sizeof(double) * (size_t)nC * p, s));
+      CK(cudaMemsetAsync(G[b], 0, sizeof(double) * (size_t)p * nC, s));
       double* amax = scratch.alloc<double>(1);
       // E(P,P) = [[X(i,i), U_i], [V_i^T, 0]]
-      cps.push_back(cp(X(st, lv, i, i), a, R.LU, p, a, a));
-      cps.push_back(cp(st.U[i], a, R.LU + (size_t)a * p, p, a, r));
-      cps.push_back(cp(st.V[i], a, R.LU + a, p, r, a, 1));
-      cps.push_back(cp_zero(R.LU + a + (size_t)a * p, p, r, r));
+      cps.push_back(cp(X(st, lv, i, i), a, LU[b], p, a, a));
+      cps.push_back(cp(st.U[i], a, LU[b] + (size_t)a * p, p, a, r));
+      cps.push_back(cp(st.V[i], a, LU[b] + a, p, r, a, 1));
+      cps.push_back(cp_zero(LU[b] + a + (size_t)a * p, p, r, r));
       for (const BlockRef& B : R.blk) {
         if (B.kind == 'y' && B.box == i) {
-          cps.push_back(cp_eye(R.G + a + (size_t)B.off * p, p, r, -1.0));
-          cps.push_back(cp_eye(R.ERP + B.off + (size_t)a * nC, nC, r, -1.0));
+          cps.push_back(cp_eye(G[b] + a + (size_t)B.off * p, p, r, -1.0));
+          cps.push_back(cp_eye(ERP[b] + B.off + (size_t)a * nC, nC, r, -1.0));
         } else {
-          cps.push_back(cp(X(st, lv, i, B.box), a, R.G + (size_t)B.off * p, p, a, B.dim));
+          cps.push_back(cp(X(st, lv, i, B.box), a, G[b] + (size_t)B.off * p, p, a, B.dim));
           const int ldj = st.a[B.box];
-          cps.push_back(cp(X(st, lv, B.box, i), ldj, R.ERP + B.off, nC, B.dim, a));
+          cps.push_back(cp(X(st, lv, B.box, i), ldj, ERP[b] + B.off, nC, B.dim, a));
         }
       }
-      lus.push_back({R.LU, p, p, R.piv, R.info, amax});
-      rss.push_back({R.LU, p, p, R.piv, R.G, p, nC});
+      // W starts as [I_a; 0] and is solved in place with the LU
+      R.W = f->store.alloc<double>((size_t)p * std::max(a, 1));
+      R.F = f->store.alloc<double>((size_t)nC * std::max(a, 1));
+      R.Ga = f->store.alloc<double>((size_t)std::max(a, 1) * nC);
+      cps.push_back(cp_eye(R.W, p, a, 1.0));
+      cps.push_back(cp_zero(R.W + a, p, r, a));
+      lus.push_back({LU[b], p, p, piv[b], R.info, amax});
+      rss.push_back({LU[b], p, p, piv[b], G[b], p, nC});
+      rss.push_back({LU[b], p, p, piv[b], R.W, p, a});
       S[b] = scratch.alloc<double>((size_t)nC * nC);
-      gs.push_back(gm(R.ERP, nC, 0, R.G, p, 0, S[b], nC, nC, nC, p, 1.0, 0.0));
+      gs.push_back(gm(ERP[b], nC, 0, G[b], p, 0, S[b], nC, nC, nC, p, 1.0, 0.0));
       f->info.flops_lu += 2.0 / 3.0 * p * (double)p * p;
-      f->info.flops_trsm += 2.0 * p * (double)p * nC;
-      f->info.flops_schur += 2.0 * nC * (double)p * nC;
+      f->info.flops_trsm += 2.0 * p * (double)p * (nC + a);
+      f->info.flops_schur += 2.0 * nC * (double)p * (nC + a);
     }
     run_copies(scratch, cps, s);
+    if (checking()) {
+      std::vector<std::pair<const double*, size_t>> v;
+      for (int b = 0; b < nbx; b++) {
+        v.push_back({LU[b], (size_t)recs[b].p * recs[b].p});
+        v.push_back({G[b], (size_t)recs[b].p * recs[b].nC});
+        v.push_back({ERP[b], (size_t)recs[b].nC * recs[b].p});
+      }
+      check_finite("pivot inputs", lv.l, boxes, v, s);
+    }
     run_getrf(scratch, lus, s);
     run_getrs(scratch, rss, s);
+    if (checking()) {
+      std::vector<std::pair<const double*, size_t>> v;
+      for (int b = 0; b < nbx; b++) {
+        v.push_back({LU[b], (size_t)recs[b].p * recs[b].p});
+        v.push_back({G[b], (size_t)recs[b].p * recs[b].nC});
+      }
+      check_finite("LU and G", lv.l, boxes, v, s);
+    }
+    // the substitution blocks: F = E(R,P) W, Ga = G[0:a, :]
+    {
+      std::vector<GemmTask> fg;
+      std::vector<CopyTask> gc;
+      for (int b = 0; b < nbx; b++) {
+        const FRec& R = recs[b];
+        fg.push_back(gm(ERP[b], R.nC, 0, R.W, R.p, 0, R.F, R.nC, R.nC, R.a, R.p, 1.0, 0.0));
+        gc.push_back(cp(G[b], R.p, R.Ga, std::max(R.a, 1), R.a, R.nC));
+      }
+      run_gemms(scratch, fg, s);
+      run_copies(scratch, gc, s);
+    }
     // Schur products S = E(R,P) G: FP64, or the tensor cores in the
     // mixed-precision modes (a wait that runs out counts in d_counters[1])
     const int prec = sys->opt.schur;
@@ -501,6 +573,11 @@ struct Factorizer {
       run_gemms_tc(scratch, gs, prec == IFMM_P_FP32, d_counters + 1, s);
     else
       run_gemms(scratch, gs, s);
+    if (checking()) {
+      std::vector<std::pair<const double*, size_t>> v;
+      for (int b = 0; b < nbx; b++) v.push_back({S[b], (size_t)recs[b].nC * recs[b].nC});
+      check_finite("Schur products", lv.l, boxes, v, s);
+    }
     // scatter -S into edges; collect well-separated fill
     struct Fill { int b, rb, cb; };
     std::vector<Fill> fills;
@@ -609,14 +686,34 @@ struct Factorizer {
       }
       rt.push_back({sU[t], sV[t], kk[t], st.rcap[j], d_r + t, d_counters});
     }
+    if (checking()) {
+      std::vector<std::pair<const double*, size_t>> v;
+      for (int t = 0; t < nJ; t++) {
+        v.push_back({MU[t], (size_t)st.a[J[t]] * wU[t]});
+        if (!sym) v.push_back({MV[t], (size_t)st.a[J[t]] * wV[t]});
+      }
+      check_finite("recompression inputs", lv.l, J, v, s);
+    }
     run_svd_left(scratch, svd, s);
     // randomised tasks, grouped by their common k
     std::map<int, std::vector<RsvdTask>> byk;
     for (auto& T : rsvd) byk[T.k].push_back(T);
     for (auto& kv : byk) run_rsvd_left(scratch, kv.second, s);
+    if (checking()) {
+      std::vector<std::pair<const double*, size_t>> v;
+      for (int t = 0; t < nJ; t++) {
+        v.push_back({WU[t], (size_t)st.a[J[t]] * kk[t]});
+        v.push_back({sU[t], (size_t)kk[t]});
+      }
+      check_finite("recompression SVD", lv.l, J, v, s);
+    }
     const RankTask* drt = upload(scratch, rt, s);
     launch_rank(drt, nJ, tau, s);
     std::vector<int> rn = read_ints(d_r, nJ);
+    if (tracing() && checking())
+      for (int t = 0; t < nJ; t++)
+        TRACE("[ifmm-check] level %d box %d: a %d, rank %d -> %d, width %d\n", lv.l, J[t],
+              st.a[J[t]], st.r[J[t]], rn[t], wU[t]);
     // r_j = U_hat^T U_old, t_j = V_hat^T V_old
     std::vector<double*> rm(nJ), tm(nJ);
     std::vector<GemmTask> g;
@@ -963,6 +1060,20 @@ ifmm_factorization* factor_create(ifmm_system* sys, cudaStream_t s) {
       CK(cudaStreamSynchronize(s));
     }
     f->info.singular_pivots = sing;
+    if (sing > 0 && tracing()) {  // which pivot blocks failed, and at which column
+      for (const FRec& R : f->recs) {
+        int v = 0;
+        CK(cudaMemcpy(&v, R.info, sizeof(int), cudaMemcpyDeviceToHost));
+        if (v != 0)
+          TRACE("[ifmm] singular pivot: level %d box %d (a %d, r %d, p %d) at column %d\n", R.l,
+                R.i, R.a, R.r, R.p, v);
+      }
+      for (int* p : {f->top_info, f->dense_info}) {
+        int v = 0;
+        if (p) CK(cudaMemcpy(&v, p, sizeof(int), cudaMemcpyDeviceToHost));
+        if (v != 0) TRACE("[ifmm] singular pivot in the top / dense LU at column %d\n", v);
+      }
+    }
     f->info.factor_bytes = (long long)f->store.held;
     return f;
   } catch (...) {

@@ -12,13 +12,19 @@ struct BlockRef {
   char kind;  // 'x': xtilde_j of a box not yet eliminated; 'y': ybar_h of an eliminated one
   int box, dim, off;
 };
+// The substitution phase needs, per box, three blocks derived from the
+// pivot block's LU (kept in the factorisation; E(P,P), E(R,P) and G itself
+// live only while their colour is eliminated):
+//   W  = E(P,P)^-1 [I_a; 0]          (p x a): w = W b_i        (RHS of the pivot set)
+//   F  = E(R,P) W                    (nC x a): b_R -= F b_i    (right-hand-side update)
+//   Ga = (E(P,P)^-1 E(P,C))[0:a, :]  (a x nC): x_i = w[0:a] - Ga x_C
+// (the z rows of the pivot set are never read by another box).
 struct FRec {
   int l, i, a, r, p, nC, colour;
-  double* LU;
-  int* piv;
-  int* info;
-  double* ERP;  // nC x p, ld nC
-  double* G;    // p x nC, ld p: E(P,P)^-1 E(P,C)
+  int* info;     // pivot test of the LU (0: passed)
+  double* W;     // p x a, ld p
+  double* F;     // nC x a, ld nC
+  double* Ga;    // a x nC, ld a
   std::vector<BlockRef> blk;
 };
 
@@ -42,6 +48,30 @@ struct SolvePlan {
   GraphCache graph;  // the steps (and the ybar clears) as one graph
 };
 
+// FP32 copies of the substitution blocks and the top system's inverse, made
+// on first use by the reduced-precision sweeps.
+struct F32Data {
+  Arena mem;
+  std::vector<const float*> W, F, Ga;  // per record
+  const float* top_inv = nullptr;      // top_n x top_n (or the dense N x N inverse)
+  bool ready = false;
+};
+
+// Reduced-precision substitution plan (FP32 vectors and blocks).
+struct SolvePlan32 {
+  int cap = 0;
+  Arena mem;
+  float* xt = nullptr;        // tree-order RHS / solution at the leaves, ld N
+  float* xt2 = nullptr;       // dense system only: the solution
+  float* top_tmp = nullptr;   // copy of the top right-hand side
+  std::vector<float*> ybar;
+  std::vector<long long> nybar;
+  std::vector<float*> w;
+  std::vector<SpmmPlanF> steps;
+  Arena task_mem;
+  GraphCache graph;
+};
+
 }  // namespace ifmm
 
 struct ifmm_factorization {
@@ -62,9 +92,12 @@ struct ifmm_factorization {
   // substitution plans by right-hand-side count (built on first use; a plan is
   // specific to its column count, so alternating batch widths keep theirs)
   std::map<int, std::unique_ptr<ifmm::SolvePlan>> plans;
+  ifmm::F32Data f32;
+  std::map<int, std::unique_ptr<ifmm::SolvePlan32>> plans32;
   size_t plan_bytes() const {
-    size_t b = 0;
+    size_t b = f32.mem.held;
     for (auto& kv : plans) b += kv.second->mem.held + kv.second->task_mem.held;
+    for (auto& kv : plans32) b += kv.second->mem.held + kv.second->task_mem.held;
     return b;
   }
 };
@@ -73,7 +106,18 @@ namespace ifmm {
 ifmm_factorization* factor_create(ifmm_system* sys, cudaStream_t s);
 void factor_solve(ifmm_factorization* f, const double* b, long long ldb, double* x,
                   long long ldx, int nrhs, cudaStream_t s);
+// The same substitution with FP32 blocks and vectors (b, x still FP64).
+void factor_solve_f32(ifmm_factorization* f, const double* b, long long ldb, double* x,
+                      long long ldx, int nrhs, cudaStream_t s);
+// Builds the FP32 copies (allocating); called by the first FP32 solve.
+void factor_prepare_f32(ifmm_factorization* f, cudaStream_t s);
+struct GmresOpts {
+  int side = IFMM_GMRES_RIGHT;  // ifmm_gmres_side
+  int refine = 2;               // restarts from x when the true residual misses tol
+  int precond_fp32 = 0;         // substitution sweeps in FP32 (flexible GMRES only)
+};
 ifmm_status gmres_run(ifmm_system* sys, ifmm_factorization* fac, int mode, const double* b,
                       double* x, int nrhs, long long ld, double tol, int maxit,
-                      ifmm_gmres_report* rep, cudaStream_t s, Arena* workspace = nullptr);
+                      ifmm_gmres_report* rep, cudaStream_t s, Arena* workspace = nullptr,
+                      const GmresOpts& opt = GmresOpts());
 }  // namespace ifmm

@@ -369,7 +369,7 @@ void run_svd_left(Arena& ar, const std::vector<SvdTask>& tasks, cudaStream_t s);
 // part, 2 a^2 w per task, is counted at launch).
 unsigned long long svd_jacobi_flops_take();
 
-// Randomised left SVD for blocks with a > 144 rows: top k left singular
+// Randomised left SVD (Sec. 2.4) for blocks taller than rsvd_rows: top k left singular
 // vectors W (a x k, ld a) and values sigma (k); every task of a call has the same k.
 struct RsvdTask {
   const double* M;
@@ -379,11 +379,10 @@ struct RsvdTask {
   double* sigma;
 };
 void run_rsvd_left(Arena& ar, const std::vector<RsvdTask>& tasks, cudaStream_t s);
-constexpr int SVD_EXACT_MAX_A = 144;  // largest k of the randomised SVD
 constexpr int SVD_SMEM_A = 160;       // largest block the shared-memory SVD takes
 constexpr int SVD_SMEM_BUDGET = 29000;  // doubles of dynamic shared memory per SVD CTA
 constexpr int RSVD_ROWS_DEFAULT = 160;  // truncated blocks taller than this use run_rsvd_left
-constexpr int RSVD_OVERSAMPLE = 16;
+constexpr int RSVD_OVERSAMPLE = 16;  // oversampling p of the randomised SVD (Sec. 2.4)
 unsigned long long rsvd_seed(int level, int box, int side);
 // inv[c] = 1 / s[c] where s[c] > 1e-10 s[0], else 0
 struct InvSigma {
@@ -455,5 +454,47 @@ struct SpmmPlan {
 SpmmPlan plan_spmm(Arena& ar, const std::vector<SpRow>& rows, const std::vector<SpEnt>& ents,
                    int cap, cudaStream_t s);
 void launch_spmm(const SpmmPlan& p, int nrhs, cudaStream_t s);
+
+// FP32 block-row products (the reduced-precision substitution sweeps):
+// y = beta y + sum_e alpha_e A_e x_e, A non-transposed (or nullptr: identity).
+struct SpRowF {
+  float* y;
+  long long ldy;
+  int m;
+  int e0, ne;
+  float beta;
+};
+struct SpEntF {
+  const float* A;
+  const float* x;
+  long long ldx;
+  int lda, k;
+  float alpha;
+};
+struct SpmmPlanF {
+  const SpRowF* rows = nullptr;
+  const SpEntF* ents = nullptr;
+  const SpJob* jobs = nullptr;
+  const SpSeg* segs = nullptr;
+  const SpRed* reds = nullptr;
+  int njobs = 0, nreds = 0;
+  float* part = nullptr;
+  long long part_ld = 0;
+  int cap = 0;
+  double flops = 0.0, bytes = 0.0;  // flops per right-hand side; bytes per pass
+};
+SpmmPlanF plan_spmm_f32(Arena& ar, const std::vector<SpRowF>& rows,
+                        const std::vector<SpEntF>& ents, int cap, cudaStream_t s);
+void launch_spmm_f32(const SpmmPlanF& p, int nrhs, cudaStream_t s);
+void launch_gather_rows_f32(const long long* perm, long long N, const double* in, long long ldi,
+                            float* out, long long ldo, int ncols, cudaStream_t s);
+void launch_scatter_rows_f32(const long long* perm, long long N, const float* in, long long ldi,
+                             double* out, long long ldo, int ncols, cudaStream_t s);
+struct NarrowTask {
+  const double* src;
+  float* dst;
+  long long n;
+};
+void launch_narrow(Arena& ar, const std::vector<NarrowTask>& v, cudaStream_t s);
 
 }  // namespace ifmm

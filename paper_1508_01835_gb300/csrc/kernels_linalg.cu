@@ -771,7 +771,9 @@ __device__ inline double group_sum(double v) {
 
 __device__ inline Refl make_refl(double x0, double sq) {
   Refl r;
-  if (sq == 0.0) {  // nothing to annihilate: identity (beta = 0)
+  // nothing to annihilate (or entries so small that beta = -1 / (alpha v0)
+  // would overflow: below 1e-140 in norm they cannot matter): identity
+  if (!(sq > 1e-280)) {
     r.alpha = x0; r.v0 = 0.0; r.beta = 0.0;
     return r;
   }
@@ -927,8 +929,10 @@ __device__ unsigned long long jacobi_columns(double* L, int lda, int a, double* 
               dsc[r2] = dq * c;
               dinv[p] = ip * ic;
               dinv[r2] = iq * ic;
+              // carried squared norms: exact arithmetic keeps both >= 0, rounding
+              // can push a nearly zero column's below zero
               nr[p] = fmax(fma(-t, g, al), 0.0);
-              nr[r2] = fma(t, g, be);
+              nr[r2] = fmax(fma(t, g, be), 0.0);
               *flag = 1;
               atomicAdd(nrot, 1u);
             }
@@ -1003,7 +1007,7 @@ __global__ void __launch_bounds__(512) k_svd_left(const SvdTask* __restrict__ ta
   // sigma_j = |L_j|; order by decreasing sigma (ties: lower column first).
   // The chunk area (>= a doubles) is free now and holds the column norms.
   double* sg = v.C;
-  for (int j = threadIdx.x; j < a; j += blockDim.x) sg[j] = sqrt(aux[j]);
+  for (int j = threadIdx.x; j < a; j += blockDim.x) sg[j] = sqrt(fmax(aux[j], 0.0));
   __syncthreads();
   double smax = 0.0;
   for (int j = 0; j < a; j++) smax = fmax(smax, sg[j]);
@@ -1167,7 +1171,8 @@ __global__ void k_fill_uniform(double* __restrict__ O, long long n, unsigned lon
 
 
 // inv[c] = 1 / s[c] where s[c] > 1e-10 s[0], else 0: drops numerically null
-// directions (above the SVD's basis-completion threshold 1e-13 a s[0], a <= 144)
+// directions (above the SVD's basis-completion threshold 1e-13 a s[0] for the
+// k <= 1000 rows these products have)
 __global__ void k_inv_sigma(const InvSigma* __restrict__ t, int n) {
   const int i = blockIdx.x;
   if (i >= n) return;
@@ -1240,8 +1245,8 @@ void run_rsvd_left(Arena& ar, const std::vector<RsvdTask>& tasks, cudaStream_t s
   // tasks are grouped by k (all tasks of one call share k)
   const int k = tasks[0].k;
   for (auto& t : tasks)
-    if (t.k != k || t.k > SVD_EXACT_MAX_A || t.k > t.a)
-      throw Error(IFMM_ERR_CUDA, "internal: randomised SVD tasks need a common k <= 144, k <= a");
+    if (t.k != k || t.k < 1 || t.k > t.a)
+      throw Error(IFMM_ERR_CUDA, "internal: randomised SVD tasks need a common k, 1 <= k <= a");
   std::vector<double*> Om(nt), Y(nt), Q(nt), Z(nt), Qz(nt), B(nt), WB(nt);
   std::vector<GemmTask> g;
   for (int t = 0; t < nt; t++) {

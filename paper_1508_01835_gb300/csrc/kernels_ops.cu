@@ -246,33 +246,21 @@ __global__ void __launch_bounds__(256) k_spmm_reduce(const SpRow* __restrict__ r
     }
 }
 
-SpmmPlan plan_spmm(Arena& ar, const std::vector<SpRow>& rows, const std::vector<SpEnt>& ents,
-                   int cap, cudaStream_t s) {
-  SpmmPlan P;
-  if (rows.empty()) return P;
-  if (cap < 1) cap = 1;
-  validate_spmm(rows, ents, cap);
-  int dev = 0, nsm = 1;
-  CK(cudaGetDevice(&dev));
-  CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+// Job split shared by the FP64 and FP32 products: about four jobs per SM, no
+// job below 8192 multiply-adds per right-hand side; a row whose work exceeds
+// the target is cut into up to 64 contiguous column ranges (partial sums).
+template <class Row, class Ent>
+static void split_jobs(const std::vector<Row>& rows, const std::vector<Ent>& ents, int nsm,
+                       std::vector<SpJob>& jobs, std::vector<SpSeg>& segs,
+                       std::vector<SpRed>& reds, long long& poff) {
   double total = 0.0;
-  for (const SpRow& R : rows) {
-    P.bytes += 8.0 * R.m;
-    for (int e = R.e0; e < R.e0 + R.ne; e++) {
-      const SpEnt& E = ents[e];
-      P.flops += 2.0 * R.m * (double)E.k;
-      P.bytes += 8.0 * E.k + (E.A ? 8.0 * R.m * (double)E.k : 0.0);
-      total += (E.A ? (double)R.m : 1.0) * E.k;
-    }
-  }
-  // about four jobs per SM; no job below 8192 multiply-adds
+  for (const Row& R : rows)
+    for (int e = R.e0; e < R.e0 + R.ne; e++)
+      total += (ents[e].A ? (double)R.m : 1.0) * ents[e].k;
   const double target = std::max(8192.0, total / (4.0 * nsm));
-  std::vector<SpJob> jobs;
-  std::vector<SpSeg> segs;
-  std::vector<SpRed> reds;
-  long long poff = 0;
+  poff = 0;
   for (int ri = 0; ri < (int)rows.size(); ri++) {
-    const SpRow& R = rows[ri];
+    const Row& R = rows[ri];
     long long K = 0;
     double work = 0.0;
     for (int e = R.e0; e < R.e0 + R.ne; e++) {
@@ -299,6 +287,34 @@ SpmmPlan plan_spmm(Arena& ar, const std::vector<SpRow>& rows, const std::vector<
     }
     if (ns > 1) poff += (long long)ns * R.m;
   }
+}
+
+static int sm_count() {
+  int dev = 0, nsm = 1;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  return nsm;
+}
+
+SpmmPlan plan_spmm(Arena& ar, const std::vector<SpRow>& rows, const std::vector<SpEnt>& ents,
+                   int cap, cudaStream_t s) {
+  SpmmPlan P;
+  if (rows.empty()) return P;
+  if (cap < 1) cap = 1;
+  validate_spmm(rows, ents, cap);
+  for (const SpRow& R : rows) {
+    P.bytes += 8.0 * R.m;
+    for (int e = R.e0; e < R.e0 + R.ne; e++) {
+      const SpEnt& E = ents[e];
+      P.flops += 2.0 * R.m * (double)E.k;
+      P.bytes += 8.0 * E.k + (E.A ? 8.0 * R.m * (double)E.k : 0.0);
+    }
+  }
+  std::vector<SpJob> jobs;
+  std::vector<SpSeg> segs;
+  std::vector<SpRed> reds;
+  long long poff = 0;
+  split_jobs(rows, ents, sm_count(), jobs, segs, reds, poff);
   P.rows = upload(ar, rows, s);
   P.ents = upload(ar, ents, s);
   P.jobs = upload(ar, jobs, s);
@@ -310,6 +326,211 @@ SpmmPlan plan_spmm(Arena& ar, const std::vector<SpRow>& rows, const std::vector<
   P.cap = cap;
   if (poff > 0) P.part = ar.alloc<double>((size_t)poff * cap);
   return P;
+}
+
+// ---------------------------------------------------------------------------
+// FP32 block-row products for the reduced-precision substitution sweeps: the
+// same job split, but every job serves all of its right-hand sides (up to 32
+// per pass) from one read of its matrix entries.  The x columns of a chunk of
+// 32 matrix columns are staged in shared memory; each warp walks a strided
+// subset of the chunk's columns for 32 output rows and keeps NB partial sums
+// per row in registers; the eight warps' sums are added through shared memory.
+// ---------------------------------------------------------------------------
+constexpr int F32_KCH = 32;
+
+template <int NB>
+__global__ void __launch_bounds__(256) k_spmm_f32(const SpRowF* __restrict__ rows,
+                                                  const SpEntF* __restrict__ ents,
+                                                  const SpJob* __restrict__ jobs,
+                                                  const SpSeg* __restrict__ segs,
+                                                  float* __restrict__ part, long long pld,
+                                                  int c0, int nb) {
+  const SpJob J = jobs[blockIdx.x];
+  const SpRowF R = rows[J.row];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __shared__ __align__(16) float xs[F32_KCH][NB + 4];
+  __shared__ float red[SPMM_WARPS][32][NB + 1];
+  for (int rt = 0; rt < R.m; rt += 32) {
+    const int r = rt + lane;
+    const bool rin = r < R.m;
+    float acc[NB];
+#pragma unroll
+    for (int c = 0; c < NB; c++) acc[c] = 0.0f;
+    for (int si = J.s0; si < J.s0 + J.ns; si++) {
+      const SpSeg G = segs[si];
+      const SpEntF E = ents[G.ent];
+      for (int kc0 = G.k0; kc0 < G.k1; kc0 += F32_KCH) {
+        const int kk = min(F32_KCH, G.k1 - kc0);
+        __syncthreads();  // the previous chunk has been read
+        for (int e = threadIdx.x; e < kk * NB; e += blockDim.x) {
+          const int col = e % kk, c = e / kk;
+          xs[col][c] = c < nb ? E.x[kc0 + col + (long long)(c0 + c) * E.ldx] : 0.0f;
+        }
+        __syncthreads();
+        if (!E.A) {  // identity: output row r takes x[r] (rows kc0 .. kc0 + kk)
+          if (wid == 0 && rin && r >= kc0 && r < kc0 + kk) {
+#pragma unroll
+            for (int c = 0; c < NB; c++) acc[c] = fmaf(E.alpha, xs[r - kc0][c], acc[c]);
+          }
+        } else if (rin) {
+          const float* a = E.A + r + (long long)kc0 * E.lda;
+          for (int col = wid; col < kk; col += SPMM_WARPS) {
+            const float av = E.alpha * a[(long long)col * E.lda];
+            const float4* xv = reinterpret_cast<const float4*>(&xs[col][0]);
+#pragma unroll
+            for (int q = 0; q < NB / 4; q++) {
+              const float4 v = xv[q];
+              acc[4 * q + 0] = fmaf(av, v.x, acc[4 * q + 0]);
+              acc[4 * q + 1] = fmaf(av, v.y, acc[4 * q + 1]);
+              acc[4 * q + 2] = fmaf(av, v.z, acc[4 * q + 2]);
+              acc[4 * q + 3] = fmaf(av, v.w, acc[4 * q + 3]);
+            }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < NB; c++) red[wid][lane][c] = acc[c];
+    __syncthreads();
+    for (int e = threadIdx.x; e < 32 * nb; e += blockDim.x) {
+      const int rl = e % 32, c = e / 32, row = rt + rl;
+      if (row < R.m) {
+        float v = 0.0f;
+#pragma unroll
+        for (int w = 0; w < SPMM_WARPS; w++) v += red[w][rl][c];
+        if (J.part < 0) {
+          float* y = R.y + (long long)(c0 + c) * R.ldy + row;
+          *y = (R.beta == 0.0f) ? v : fmaf(R.beta, *y, v);
+        } else {
+          part[J.part + row + (long long)c * pld] = v;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(256) k_spmm_f32_reduce(const SpRowF* __restrict__ rows,
+                                                         const SpRed* __restrict__ reds,
+                                                         const float* __restrict__ part,
+                                                         long long pld, int c0, int nb) {
+  const SpRed D = reds[blockIdx.x];
+  const SpRowF R = rows[D.row];
+  for (int c = 0; c < nb; c++)
+    for (int r = threadIdx.x; r < R.m; r += blockDim.x) {
+      const float* pp = part + D.base + r + (long long)c * pld;
+      float v = 0.0f;
+      for (int j = 0; j < D.nj; j++) v += pp[(long long)j * R.m];
+      float* y = R.y + (long long)(c0 + c) * R.ldy + r;
+      *y = (R.beta == 0.0f) ? v : fmaf(R.beta, *y, v);
+    }
+}
+
+SpmmPlanF plan_spmm_f32(Arena& ar, const std::vector<SpRowF>& rows,
+                        const std::vector<SpEntF>& ents, int cap, cudaStream_t s) {
+  SpmmPlanF P;
+  if (rows.empty()) return P;
+  if (cap < 1) cap = 1;
+  for (const SpRowF& R : rows) {
+    Ranges::check(R.y, sizeof(float) * ((size_t)(cap - 1) * R.ldy + R.m), "spmm32 y");
+    P.bytes += 4.0 * R.m;
+    for (int e = R.e0; e < R.e0 + R.ne; e++) {
+      const SpEntF& E = ents[e];
+      if (E.A) Ranges::check(E.A, sizeof(float) * ((size_t)(E.k - 1) * E.lda + R.m), "spmm32 A");
+      Ranges::check(E.x, sizeof(float) * ((size_t)(cap - 1) * E.ldx + E.k), "spmm32 x");
+      P.flops += 2.0 * R.m * (double)E.k;
+      P.bytes += 4.0 * E.k + (E.A ? 4.0 * R.m * (double)E.k : 0.0);
+    }
+  }
+  std::vector<SpJob> jobs;
+  std::vector<SpSeg> segs;
+  std::vector<SpRed> reds;
+  long long poff = 0;
+  split_jobs(rows, ents, sm_count(), jobs, segs, reds, poff);
+  P.rows = upload(ar, rows, s);
+  P.ents = upload(ar, ents, s);
+  P.jobs = upload(ar, jobs, s);
+  P.segs = segs.empty() ? nullptr : upload(ar, segs, s);
+  P.reds = reds.empty() ? nullptr : upload(ar, reds, s);
+  P.njobs = (int)jobs.size();
+  P.nreds = (int)reds.size();
+  P.part_ld = poff;
+  P.cap = cap;
+  if (poff > 0) P.part = ar.alloc<float>((size_t)poff * std::min(cap, 32));
+  return P;
+}
+
+void launch_spmm_f32(const SpmmPlanF& p, int nrhs, cudaStream_t s) {
+  if (p.njobs <= 0 || nrhs <= 0) return;
+  for (int c0 = 0; c0 < nrhs; c0 += 32) {
+    const int nb = std::min(32, nrhs - c0);
+    {
+      Prof pr("k_spmm_f32", p.flops * nb, p.bytes, s);
+      if (nb <= 4)
+        k_spmm_f32<4><<<p.njobs, 256, 0, s>>>(p.rows, p.ents, p.jobs, p.segs, p.part, p.part_ld, c0, nb);
+      else if (nb <= 8)
+        k_spmm_f32<8><<<p.njobs, 256, 0, s>>>(p.rows, p.ents, p.jobs, p.segs, p.part, p.part_ld, c0, nb);
+      else if (nb <= 16)
+        k_spmm_f32<16><<<p.njobs, 256, 0, s>>>(p.rows, p.ents, p.jobs, p.segs, p.part, p.part_ld, c0, nb);
+      else
+        k_spmm_f32<32><<<p.njobs, 256, 0, s>>>(p.rows, p.ents, p.jobs, p.segs, p.part, p.part_ld, c0, nb);
+      CK_LAUNCH("k_spmm_f32");
+    }
+    if (p.nreds > 0) {
+      Prof pr("k_spmm_f32_reduce", 0.0, 8.0 * p.part_ld * nb, s);
+      k_spmm_f32_reduce<<<p.nreds, 256, 0, s>>>(p.rows, p.reds, p.part, p.part_ld, c0, nb);
+      CK_LAUNCH("k_spmm_f32_reduce");
+    }
+  }
+}
+
+// FP64 <-> FP32 copies with a row permutation (the reduced-precision sweeps
+// read b and write x in FP64, user order; they work in FP32, tree order).
+__global__ void k_gather_rows_f32(const long long* __restrict__ perm, long long N,
+                                  const double* __restrict__ in, long long ldi,
+                                  float* __restrict__ out, long long ldo, int ncols) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N) return;
+  const long long src = perm[t];
+  for (int c = 0; c < ncols; c++) out[t + c * ldo] = (float)in[src + c * ldi];
+}
+__global__ void k_scatter_rows_f32(const long long* __restrict__ perm, long long N,
+                                   const float* __restrict__ in, long long ldi,
+                                   double* __restrict__ out, long long ldo, int ncols) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N) return;
+  const long long dst = perm[t];
+  for (int c = 0; c < ncols; c++) out[dst + c * ldo] = (double)in[t + c * ldi];
+}
+void launch_gather_rows_f32(const long long* perm, long long N, const double* in, long long ldi,
+                            float* out, long long ldo, int ncols, cudaStream_t s) {
+  if (N <= 0) return;
+  k_gather_rows_f32<<<(int)((N + 255) / 256), 256, 0, s>>>(perm, N, in, ldi, out, ldo, ncols);
+  CK_LAUNCH("k_gather_rows_f32");
+}
+void launch_scatter_rows_f32(const long long* perm, long long N, const float* in, long long ldi,
+                             double* out, long long ldo, int ncols, cudaStream_t s) {
+  if (N <= 0) return;
+  k_scatter_rows_f32<<<(int)((N + 255) / 256), 256, 0, s>>>(perm, N, in, ldi, out, ldo, ncols);
+  CK_LAUNCH("k_scatter_rows_f32");
+}
+
+// Element-wise FP64 -> FP32 narrowing of a list of arrays (one CTA per array).
+__global__ void k_narrow(const NarrowTask* __restrict__ t) {
+  const NarrowTask T = t[blockIdx.x];
+  for (long long e = threadIdx.x; e < T.n; e += blockDim.x) T.dst[e] = (float)T.src[e];
+}
+void launch_narrow(Arena& ar, const std::vector<NarrowTask>& v, cudaStream_t s) {
+  std::vector<NarrowTask> keep;
+  for (const NarrowTask& t : v)
+    if (t.n > 0) {
+      Ranges::check(t.src, sizeof(double) * t.n, "narrow src");
+      Ranges::check(t.dst, sizeof(float) * t.n, "narrow dst");
+      keep.push_back(t);
+    }
+  if (keep.empty()) return;
+  k_narrow<<<(int)keep.size(), 256, 0, s>>>(upload(ar, keep, s));
+  CK_LAUNCH("k_narrow");
 }
 
 void launch_spmm(const SpmmPlan& p, int nrhs, cudaStream_t s) {

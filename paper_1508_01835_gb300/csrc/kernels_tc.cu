@@ -22,7 +22,12 @@
 //
 // Every wait on an mbarrier is bounded; a wait that runs out records an error
 // code in *err and the CTA still drains its own tensor-core work (again with a
-// bound) and frees its tensor memory before it returns.
+// bound) and frees its tensor memory before it returns.  A pipeline wait that
+// takes more than `soft_polls` polls is also recorded in *err (the caller
+// reports IFMM_ERR_TIMEOUT) but keeps waiting up to the hard bound; the soft
+// limit equals the hard one unless IFMM_TC_SOFT_WAIT_POLLS lowers it (then the
+// first polls are non-blocking test_wait), which is how a test makes a wait run
+// out without leaving any work in flight.
 #include "internal.cuh"
 
 namespace ifmm {
@@ -94,6 +99,34 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   for (long long it = 0; it < SPIN_LIMIT; it++)
     if (mbar_try(bar, parity)) return true;
   return false;
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Pipeline wait with a reporting limit.  With a limit below the hard bound the
+// wait first makes `soft` non-blocking polls (test_wait); if the phase is not
+// complete by then the wait counts as late (*late = true, reported as
+// IFMM_ERR_TIMEOUT) and continues with the blocking polls up to the hard
+// bound, so the pipeline's phase accounting stays exact and no tensor memory
+// is freed while its MMAs run.  Returns false only when the hard bound ran out.
+__device__ __forceinline__ bool mbar_wait_soft(uint64_t* bar, uint32_t parity, long long soft,
+                                               bool* late) {
+  if (soft < SPIN_LIMIT) {
+    for (long long it = 0; it < soft; it++)
+      if (mbar_test(bar, parity)) return true;
+    *late = true;
+  }
+  return mbar_wait(bar, parity);
 }
 
 __device__ __forceinline__ void fence_before() {
@@ -229,7 +262,8 @@ __device__ __forceinline__ void load_slice(const double* __restrict__ X, int ld,
 // A lo, B lo} slices (the lo slices only in split mode) + barriers.
 __global__ void __launch_bounds__(tc::NTHREADS) k_gemm_tc(const GemmTask* __restrict__ tasks,
                                                           const GemmTile* __restrict__ tiles,
-                                                          int split, int* __restrict__ err) {
+                                                          int split, int* __restrict__ err,
+                                                          long long soft_polls) {
   using namespace tc;
   extern __shared__ __align__(1024) char smem_raw[];
   // 1024-byte alignment of the operand area
@@ -260,12 +294,12 @@ __global__ void __launch_bounds__(tc::NTHREADS) k_gemm_tc(const GemmTask* __rest
   const uint32_t tmem = tmem_base_s;
 
   const int nk = (t.K + BK - 1) / BK;
-  bool ok = true;
+  bool ok = true, late = false;
   for (int kt = 0; kt < nk; kt++) {
     const int s = kt & 1;
     if (kt >= 2) {
       // the MMAs that read this stage two slices ago must be done
-      if (!mbar_wait(&bar[s], (uint32_t)(((kt - 2) >> 1) & 1))) ok = false;
+      if (!mbar_wait_soft(&bar[s], (uint32_t)(((kt - 2) >> 1) & 1), soft_polls, &late)) ok = false;
     }
     char* st = stage[s];
     load_slice(t.A, t.lda, t.transA, t.M, t.K, tl.m0, kt * BK, st, split ? st + 2 * SLICE_BYTES : nullptr,
@@ -296,8 +330,9 @@ __global__ void __launch_bounds__(tc::NTHREADS) k_gemm_tc(const GemmTask* __rest
   // wait for the last commit of each stage (every thread, so all see the result)
   for (int s = 0; s < 2; s++) {
     const int n_s = (nk - s + 1) / 2;  // commits on stage s
-    if (n_s > 0 && !mbar_wait(&bar[s], (uint32_t)((n_s - 1) & 1))) ok = false;
+    if (n_s > 0 && !mbar_wait_soft(&bar[s], (uint32_t)((n_s - 1) & 1), soft_polls, &late)) ok = false;
   }
+  if (late) atomicExch(err, 1);  // results are complete; the lateness is reported
   // one verdict for the whole CTA: the epilogue's tcgen05.ld is warp-collective
   ok = __syncthreads_and(ok) != 0;
   fence_after();
@@ -367,8 +402,14 @@ void launch_gemm_tc(const GemmTask* d_tasks, const GemmTile* d_tiles, int ntiles
   if (ntiles <= 0) return;
   set_max_dynamic_smem((const void*)k_gemm_tc, (int)gemm_tc_smem(true));
   Prof p(split ? "k_gemm_tc_3xtf32" : "k_gemm_tc_tf32", flops, 0.0, s);
+  // test hook: a lower reporting limit for the pipeline waits (see k_gemm_tc)
+  long long soft = tc::SPIN_LIMIT;
+  if (const char* e = std::getenv("IFMM_TC_SOFT_WAIT_POLLS")) {
+    const long long v = std::atoll(e);
+    if (v >= 1) soft = std::min(v, tc::SPIN_LIMIT);
+  }
   k_gemm_tc<<<ntiles, tc::NTHREADS, gemm_tc_smem(split), s>>>(d_tasks, d_tiles, split ? 1 : 0,
-                                                             d_err);
+                                                             d_err, soft);
   CK_LAUNCH("k_gemm_tc");
 }
 

@@ -9,7 +9,7 @@
 #include <mutex>
 #include <set>
 
-#include "internal.cuh"
+#include "system.cuh"
 
 namespace ifmm {
 
@@ -202,3 +202,77 @@ void run_graph(GraphCache& g, long long key, const char* name, cudaStream_t s,
 }
 
 }  // namespace ifmm
+
+// ---------------------------------------------------------------------------
+// Peak arithmetic rates of this GPU, measured: every thread runs NCHAIN
+// independent FMA chains of `iters` steps (so the pipe, not the latency,
+// bounds the rate), over a grid of 8 CTAs of 256 threads per SM; rate =
+// 2 x FMAs / CUDA-event time of the launch (after one warm-up launch).
+// ---------------------------------------------------------------------------
+namespace ifmm {
+template <class T>
+__global__ void __launch_bounds__(256) k_fma_rate(T* out, int iters, T seed) {
+  constexpr int NCHAIN = 8;
+  T a[NCHAIN];
+#pragma unroll
+  for (int c = 0; c < NCHAIN; c++) a[c] = seed + (T)(threadIdx.x + c);
+  const T m = (T)0.999999, d = (T)1e-7;
+  for (int i = 0; i < iters; i++) {
+#pragma unroll
+    for (int c = 0; c < NCHAIN; c++) a[c] = a[c] * m + d;
+  }
+  T s = 0;
+#pragma unroll
+  for (int c = 0; c < NCHAIN; c++) s += a[c];
+  if (s == (T)-1.2345) out[0] = s;  // never true: keeps the chains live
+}
+
+template <class T>
+static double fma_rate(int iters) {
+  int dev = 0, nsm = 1;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  T* out = nullptr;
+  CK(cudaMalloc(&out, sizeof(T)));
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  const int grid = nsm * 8;
+  k_fma_rate<T><<<grid, 256>>>(out, iters / 10, (T)1);
+  CK_LAUNCH("k_fma_rate");
+  CK(cudaEventRecord(a));
+  k_fma_rate<T><<<grid, 256>>>(out, iters, (T)1);
+  CK_LAUNCH("k_fma_rate");
+  CK(cudaEventRecord(b));
+  CK(cudaEventSynchronize(b));
+  float ms = 0.0f;
+  CK(cudaEventElapsedTime(&ms, a, b));
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(out);
+  const double fmas = (double)grid * 256 * 8 * (double)iters;
+  return 2.0 * fmas / (ms * 1e-3) / 1e12;
+}
+}  // namespace ifmm
+
+extern "C" ifmm_status ifmm_measure_peaks(ifmm_ctx* ctx, double* fp64_tflops, double* fp32_tflops) {
+  if (!ctx || !fp64_tflops || !fp32_tflops) return IFMM_ERR_INVALID_ARG;
+  try {
+    CK(cudaSetDevice(ctx->device));
+    *fp64_tflops = ifmm::fma_rate<double>(1 << 14);
+    *fp32_tflops = ifmm::fma_rate<float>(1 << 17);
+    return IFMM_OK;
+  } catch (const ifmm::Error& e) {
+    ctx->last_error = e.what();
+    return e.st;
+  } catch (const std::exception& e) {
+    ctx->last_error = e.what();
+    return IFMM_ERR_CUDA;
+  }
+}
+
+extern "C" ifmm_status ifmm_launch_count(unsigned long long* launches) {
+  if (!launches) return IFMM_ERR_INVALID_ARG;
+  *launches = ifmm::launches_total();
+  return IFMM_OK;
+}

@@ -3,18 +3,22 @@
 //
 // Some callers cannot allocate device memory while they run: a host
 // application that owns a fixed device pool and forbids further cudaMalloc,
-// or a real-time loop that must not stall on the allocator.  For them this entry point takes its scratch (the tree lists it
-// needs and the multipole / local coefficients) from one file-scope device
-// array of STATIC_SCRATCH_BYTES, which every GPU that loads the library holds
-// until the process exits.  The caller passes x and y; the system's operators
-// (allocated when the system was created) are read in place.
+// or a real-time loop that must not stall on the allocator.  For them this
+// entry point takes its scratch (the multipole / local coefficients and x, y
+// in tree order) from one file-scope device array of STATIC_SCRATCH_BYTES,
+// which every GPU that loads the library holds until the process exits.  The
+// caller passes x and y; the system's operators and lists (allocated when the
+// system was created) are read in place.
 //
 // Set-up: the first call on a device looks up the array's device address with
 // cudaGetSymbolAddress while that device is current; make that first call
 // before any stream capture.  All calls share the array and it keeps the last
 // call's contents; calls that overlap on the GPU race with each other.  No
-// part of the array has to start at zero: each call uploads its lists and
-// writes every coefficient before reading it.
+// part of the array has to start at zero: each call writes every coefficient
+// before reading it.  The tree lists the kernels walk are copied to the device
+// once, when the system is created (build_static_lists), so a call copies
+// nothing from the host and does no per-call host work beyond its launches.
+#include <cstring>
 #include <map>
 #include <mutex>
 
@@ -37,9 +41,9 @@ static unsigned char* static_scratch(int device) {
   return static_cast<unsigned char*>(p);
 }
 
-// Per-depth view of the lists inside the static array.
+// Per-depth view: the system's lists and this call's coefficients (in the array).
 struct SLevel {
-  const int* child_begin;  // nb + 1 entries: children of box p are [child_begin[p], child_begin[p+1])
+  const int* child_begin;  // nb + 1: children of box p are [child_begin[p], child_begin[p+1])
   const int* cpos;         // nb: position of the box inside its parent (0 .. 2^D - 1)
   const int* parent;       // nb
   const int* far_ptr;      // nb + 1
@@ -149,6 +153,65 @@ struct Carver {
   }
 };
 
+// The lists of every depth, packed into one block of the system's memory.
+void build_static_lists(ifmm_system* sys, cudaStream_t s) {
+  const int L = sys->L, dim = sys->dim;
+  std::vector<unsigned char> img;
+  auto put = [&](const void* src, size_t n, size_t elem) {
+    const size_t off = img.size();
+    img.resize(off + ((n * elem + 255) & ~size_t(255)), 0);
+    if (n) std::memcpy(img.data() + off, src, n * elem);
+    return off;
+  };
+  struct Off { size_t cb, cpos, par, fptr, fidx, foff; };
+  std::vector<Off> lo(L + 1);
+  for (int l = 2; l <= L; l++) {
+    const LevelTopo& v = sys->lv[l];
+    std::vector<int> cb(v.nb + 1), cpos(v.nb), par(v.nb), foff(v.far.size());
+    for (int p = 0; p < v.nb; p++) cb[p] = (l < L) ? v.cb[p] : 0;
+    cb[v.nb] = (l < L) ? (v.nb ? v.ce[v.nb - 1] : 0) : 0;
+    for (int i = 0; i < v.nb; i++) {
+      cpos[i] = v.child_pos(i, dim);
+      par[i] = v.parent.empty() ? 0 : v.parent[i];
+      for (int e = v.far_ptr[i]; e < v.far_ptr[i + 1]; e++) foff[e] = v.m2l_offset(i, v.far[e], dim);
+    }
+    lo[l].cb = put(cb.data(), cb.size(), 4);
+    lo[l].cpos = put(cpos.data(), cpos.size(), 4);
+    lo[l].par = put(par.data(), par.size(), 4);
+    lo[l].fptr = put(v.far_ptr.data(), v.far_ptr.size(), 4);
+    lo[l].fidx = put(v.far.data(), v.far.size(), 4);
+    lo[l].foff = put(foff.data(), foff.size(), 4);
+  }
+  const LevelTopo& leaf = sys->lv[L];
+  std::vector<int> p0(leaf.nb + 1);
+  for (int i = 0; i < leaf.nb; i++) p0[i] = leaf.p0[i];
+  p0[leaf.nb] = (int)sys->N;
+  const ChebOps& ops = sys->mv();
+  const size_t o_p0 = put(p0.data(), p0.size(), 4);
+  const size_t o_uoff = put(ops.uoff.data(), ops.uoff.size(), 8);
+  const size_t o_nptr = put(leaf.nbr_ptr.data(), leaf.nbr_ptr.size(), 4);
+  const size_t o_nidx = put(leaf.nbr.data(), leaf.nbr.size(), 4);
+  const size_t o_p2p = put(sys->p2p_off.data(), sys->p2p_off.size(), 8);
+  unsigned char* d = sys->mem.alloc<unsigned char>(std::max<size_t>(img.size(), 256));
+  CK(cudaMemcpyAsync(d, img.data(), img.size(), cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));  // img is a local
+  sys->static_lv.assign(L + 1, StaticLevelLists{});
+  for (int l = 2; l <= L; l++) {
+    StaticLevelLists& q = sys->static_lv[l];
+    q.child_begin = (const int*)(d + lo[l].cb);
+    q.cpos = (const int*)(d + lo[l].cpos);
+    q.parent = (const int*)(d + lo[l].par);
+    q.far_ptr = (const int*)(d + lo[l].fptr);
+    q.far_idx = (const int*)(d + lo[l].fidx);
+    q.far_off = (const int*)(d + lo[l].foff);
+  }
+  sys->static_leaf.p0 = (const int*)(d + o_p0);
+  sys->static_leaf.uoff = (const long long*)(d + o_uoff);
+  sys->static_leaf.nbr_ptr = (const int*)(d + o_nptr);
+  sys->static_leaf.nbr_idx = (const int*)(d + o_nidx);
+  sys->static_leaf.p2p_off = (const long long*)(d + o_p2p);
+}
+
 void system_matvec_static(ifmm_system* sys, const double* x, double* y, int nrhs, long long ld,
                           int device, cudaStream_t s) {
   if (nrhs <= 0) return;
@@ -157,74 +220,46 @@ void system_matvec_static(ifmm_system* sys, const double* x, double* y, int nrhs
     return;
   }
   const ChebOps& ops = sys->mv();
-  const int nd = ops.nd, L = sys->L, dim = sys->dim;
+  const int nd = ops.nd, L = sys->L;
   const long long N = sys->N;
-  // host images of the lists, laid out exactly as they will sit in the array
-  std::vector<std::vector<int>> cb(L + 1), cpos(L + 1), par(L + 1), fptr(L + 1), fidx(L + 1),
-      foff(L + 1);
+  // scratch: multipole and local coefficients of every depth, x and y in tree order
   size_t bytes = 0;
-  auto need = [&](size_t n, size_t elem) { bytes += (n * elem + 255) & ~size_t(255); };
+  auto need = [&](size_t n) { bytes += (n * sizeof(double) + 255) & ~size_t(255); };
   for (int l = 2; l <= L; l++) {
-    const LevelTopo& v = sys->lv[l];
-    cb[l].resize(v.nb + 1);
-    for (int p = 0; p < v.nb; p++) cb[l][p] = (l < L) ? v.cb[p] : 0;
-    cb[l][v.nb] = (l < L) ? (v.nb ? v.ce[v.nb - 1] : 0) : 0;
-    cpos[l].resize(v.nb);
-    par[l].resize(v.nb);
-    for (int i = 0; i < v.nb; i++) {
-      cpos[l][i] = v.child_pos(i, dim);
-      par[l][i] = v.parent.empty() ? 0 : v.parent[i];
-    }
-    fptr[l] = v.far_ptr;
-    fidx[l] = v.far;
-    foff[l].resize(v.far.size());
-    for (int i = 0; i < v.nb; i++)
-      for (int e = v.far_ptr[i]; e < v.far_ptr[i + 1]; e++) foff[l][e] = v.m2l_offset(i, v.far[e], dim);
-    need(cb[l].size(), 4); need(cpos[l].size(), 4); need(par[l].size(), 4);
-    need(fptr[l].size(), 4); need(fidx[l].size(), 4); need(foff[l].size(), 4);
-    need((size_t)v.nb * nd * nrhs, 8);  // mult
-    need((size_t)v.nb * nd * nrhs, 8);  // loc
+    need((size_t)sys->lv[l].nb * nd * nrhs);  // mult
+    need((size_t)sys->lv[l].nb * nd * nrhs);  // loc
   }
-  const LevelTopo& leaf = sys->lv[L];
-  std::vector<int> p0(leaf.nb + 1);
-  for (int i = 0; i < leaf.nb; i++) p0[i] = leaf.p0[i];
-  p0[leaf.nb] = (int)N;
-  need(p0.size(), 4); need(ops.uoff.size(), 8); need(leaf.nbr_ptr.size(), 4);
-  need(leaf.nbr.size(), 4); need(sys->p2p_off.size(), 8);
-  need((size_t)N * nrhs, 8);  // x in tree order
-  need((size_t)N * nrhs, 8);  // y in tree order
+  need((size_t)N * nrhs);  // x in tree order
+  need((size_t)N * nrhs);  // y in tree order
   if (bytes > STATIC_SCRATCH_BYTES)
     throw Error(IFMM_ERR_INVALID_ARG,
                 "fmm_matvec_static: this system and nrhs need " + std::to_string(bytes) +
                     " bytes of scratch; the static buffer holds " +
                     std::to_string(STATIC_SCRATCH_BYTES) + " (use fewer right-hand sides or fmm_matvec)");
   Carver cv{static_scratch(device)};
-  auto put = [&](const void* src, size_t n, size_t elem) {
-    unsigned char* d = cv.take<unsigned char>(n * elem);
-    if (n) CK(cudaMemcpyAsync(d, src, n * elem, cudaMemcpyHostToDevice, s));
-    return d;
-  };
   std::vector<SLevel> SL(L + 1);
   for (int l = 2; l <= L; l++) {
     SLevel& q = SL[l];
+    const StaticLevelLists& g = sys->static_lv[l];
     q.nb = sys->lv[l].nb;
-    q.child_begin = (const int*)put(cb[l].data(), cb[l].size(), 4);
-    q.cpos = (const int*)put(cpos[l].data(), cpos[l].size(), 4);
-    q.parent = (const int*)put(par[l].data(), par[l].size(), 4);
-    q.far_ptr = (const int*)put(fptr[l].data(), fptr[l].size(), 4);
-    q.far_idx = (const int*)put(fidx[l].data(), fidx[l].size(), 4);
-    q.far_off = (const int*)put(foff[l].data(), foff[l].size(), 4);
+    q.child_begin = g.child_begin;
+    q.cpos = g.cpos;
+    q.parent = g.parent;
+    q.far_ptr = g.far_ptr;
+    q.far_idx = g.far_idx;
+    q.far_off = g.far_off;
     q.m2l = ops.m2l[l];
     q.mult = cv.take<double>((size_t)q.nb * nd * nrhs);
     q.loc = cv.take<double>((size_t)q.nb * nd * nrhs);
   }
+  const LevelTopo& leaf = sys->lv[L];
   SLeaf lf;
   lf.nb = leaf.nb;
-  lf.p0 = (const int*)put(p0.data(), p0.size(), 4);
-  lf.uoff = (const long long*)put(ops.uoff.data(), ops.uoff.size(), 8);
-  lf.nbr_ptr = (const int*)put(leaf.nbr_ptr.data(), leaf.nbr_ptr.size(), 4);
-  lf.nbr_idx = (const int*)put(leaf.nbr.data(), leaf.nbr.size(), 4);
-  lf.p2p_off = (const long long*)put(sys->p2p_off.data(), sys->p2p_off.size(), 8);
+  lf.p0 = sys->static_leaf.p0;
+  lf.uoff = sys->static_leaf.uoff;
+  lf.nbr_ptr = sys->static_leaf.nbr_ptr;
+  lf.nbr_idx = sys->static_leaf.nbr_idx;
+  lf.p2p_off = sys->static_leaf.p2p_off;
   lf.U = ops.leafU;
   lf.S = sys->p2p;
   double* xt = cv.take<double>((size_t)N * nrhs);

@@ -205,6 +205,7 @@ ifmm_system* system_create(ifmm_ctx* ctx, const double* pts, bool host, long lon
     const int fn = opt->fmm_n > 0 ? opt->fmm_n : opt->cheb_n;
     sys->same_ops = (fn == opt->cheb_n);
     if (!sys->same_ops) build_ops(sys, fn, sys->ops_mv, s);
+    build_static_lists(sys, s);
     CK(cudaStreamSynchronize(s));
     return sys;
   } catch (...) {

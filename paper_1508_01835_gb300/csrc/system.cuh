@@ -62,6 +62,24 @@ struct ChebOps {
   std::vector<double*> m2l;         // per depth: 7^D blocks nd x nd (depth >= 2)
 };
 
+// Device copies of the lists the allocation-free matvec reads (built once when
+// the system is created, in the system's own memory).
+struct StaticLevelLists {
+  const int* child_begin = nullptr;  // nb + 1: children of box p are [child_begin[p], child_begin[p+1])
+  const int* cpos = nullptr;         // nb: position of the box inside its parent
+  const int* parent = nullptr;       // nb
+  const int* far_ptr = nullptr;      // nb + 1
+  const int* far_idx = nullptr;      // interaction list entries
+  const int* far_off = nullptr;      // M2L table offset of each entry
+};
+struct StaticLeafLists {
+  const int* p0 = nullptr;             // nb + 1 point offsets (tree order)
+  const long long* uoff = nullptr;     // nb: offset of U_i
+  const int* nbr_ptr = nullptr;        // nb + 1
+  const int* nbr_idx = nullptr;
+  const long long* p2p_off = nullptr;  // per neighbour entry
+};
+
 // A launch sequence of block-row products.
 struct SpPlan {
   std::vector<SpmmPlan> phases;
@@ -117,6 +135,8 @@ struct ifmm_system {
   ifmm::GraphCache fmm_graph;  // fmm_plan.run as one graph
   int fmm_cap = 0;
   double *fmm_x = nullptr, *fmm_y = nullptr;
+  std::vector<ifmm::StaticLevelLists> static_lv;  // per depth 2..L (fmm_matvec_static)
+  ifmm::StaticLeafLists static_leaf;
   double sigma0 = std::numeric_limits<double>::quiet_NaN();
   int sigma0_iters = 0;
   const ifmm::ChebOps& mv() const { return same_ops ? ops_f : ops_mv; }
@@ -130,4 +150,5 @@ void system_matvec(ifmm_system* sys, int mode, const double* x, long long ldx, d
 double system_sigma0(ifmm_system* sys, cudaStream_t s, int* iters);
 void system_matvec_static(ifmm_system* sys, const double* x, double* y, int nrhs, long long ld,
                           int device, cudaStream_t s);
+void build_static_lists(ifmm_system* sys, cudaStream_t s);
 }  // namespace ifmm

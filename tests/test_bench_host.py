@@ -1,32 +1,36 @@
 """Host logic of bench.py (no GPU): the roofline rows built from the library's
-launch profile, with the bound chosen per kernel family."""
+launch profile, each kernel placed against the pipe it fills most."""
 import pytest
 
 import bench
 
-PEAKS = {"hbm_gbs": 6685.5, "bf16_tflops": 1944.2}
+PEAKS = {"hbm_gbs": 6685.5, "bf16_tflops": 1944.2, "fp64_tflops": 1.2, "fp32_tflops": 70.0}
 
 
-def test_rooflines_per_family_dominant_and_weighted():
+def test_rooflines_bound_by_the_fullest_pipe_dominant_and_weighted():
     stats = {  # name: (launches, seconds, flops, bytes)
         "k_svd_left": (452, 10.0, 1.4e12, 0.0),
         "k_gemm_tc_3xtf32": (162, 0.8, 4.74e12, 0.0),
-        "k_spmm_job": (40, 0.6, 1e9, 3.0e12),
+        "k_spmm_job": (40, 0.6, 1e9, 3.0e12),          # bytes-heavy: HBM
+        "k_spmm_f32": (40, 0.5, 2.0e13, 1.0e12),       # 40 TFLOP/s FP32 vs 2 TB/s: FP32 ALU
         "k_gemm_fp64": (2812, 3.2, 1.6e12, 0.0),
         "(all launches)": (42822, 0.0, 0.0, 0.0),
         "graph:ifmm_solve": (20, 0.5, 1e9, 1e9),
     }
     rows, dom, weighted = bench.kernel_rooflines(stats, 21.0, PEAKS)
-    assert set(rows) == {"k_svd_left", "k_gemm_tc_3xtf32", "k_spmm_job", "k_gemm_fp64"}
+    assert set(rows) == {"k_svd_left", "k_gemm_tc_3xtf32", "k_spmm_job", "k_spmm_f32",
+                         "k_gemm_fp64"}
     assert dom["kernel"] == "k_svd_left" and dom["bound"] == "alu"
-    assert dom["achieved"] == pytest.approx(0.14) and dom["frac"] == pytest.approx(0.14 / 1.25)
-    assert dom["share_of_step"] == pytest.approx(10.0 / 21.0)
+    assert dom["achieved"] == pytest.approx(0.14) and dom["frac"] == pytest.approx(0.14 / 1.2)
+    assert dom["share"] == pytest.approx(10.0 / 21.0)
     tc = rows["k_gemm_tc_3xtf32"]
     assert tc["bound"] == "tensor" and tc["peak"] == pytest.approx(1944.2 * 1.1 / 2.25)
     assert tc["achieved"] == pytest.approx(4.74e12 / 0.8 / 1e12)
     sp = rows["k_spmm_job"]
     assert sp["bound"] == "hbm" and sp["achieved"] == pytest.approx(5000.0)
     assert sp["frac"] == pytest.approx(5000.0 / 6685.5)
+    f32 = rows["k_spmm_f32"]
+    assert f32["bound"] == "alu" and f32["peak"] == 70.0 and f32["achieved"] == pytest.approx(40.0)
     fr = [(r["s"], r["frac"]) for r in rows.values()]
     assert weighted == pytest.approx(sum(t * f for t, f in fr) / sum(t for t, _ in fr))
 
@@ -35,3 +39,9 @@ def test_rooflines_empty_profile():
     rows, dom, weighted = bench.kernel_rooflines({"(all launches)": (0, 0.0, 0.0, 0.0)}, 1.0,
                                                  PEAKS)
     assert rows == {} and dom is None and weighted is None
+
+
+def test_percentiles_and_rates():
+    assert bench._pct([3.0, 1.0, 2.0], 50) == 2.0
+    assert bench._pct(list(range(1, 101)), 99) == 99
+    assert bench.whole_job_rate(10, 2, 2000.0) == pytest.approx(10.0)

@@ -214,30 +214,184 @@ def test_gmres_cube2k_direct_matches_dense_lu(ctx):
         ifmm.ifmm_system_destroy(sys)
 
 
-@pytest.mark.parametrize("name", ["cube2k", "3lev"])
-def test_gmres_parity_with_oracle(ctx, name):
-    """FMM matvec + IFMM right preconditioner: same iteration count as the
-    oracle's GMRES (+-1), true residual <= 1e-10, same solution to 1e-8."""
-    w = CASES[name]()
-    h2 = oracle_h2(w)
-    ora = IFMM(h2, w.eps)
+def _oracle_gmres(w, h2, ora, tol, side="right"):
     b = w.rhs(1)[:, 0]
     p = h2.tree.perm
 
     def mv(v):
         return to_user(h2, h2.matvec(v[p]))
 
-    x_o, it_o, res_o = oracle_gmres(mv, b, ora.solve, 1e-10, 500)
+    x, it, res = oracle_gmres(mv, b, ora.solve, tol, 500, side=side)
+    return b, x, it
+
+
+@pytest.mark.parametrize("name", ["cube2k", "3lev", "2d", "paper"])
+def test_gmres_parity_with_oracle(ctx, name):
+    """FMM matvec + IFMM right preconditioner, both sides the same
+    non-restarted GMRES (refine = 0) run to tol 1e-13, so that kappa(A) ~ 1e6
+    of the cube recipe does not mask a difference: same iteration count as the
+    oracle's GMRES (+-1), Arnoldi estimate <= 1e-13, true residual <= 1e-10
+    (without restarts the recomputed residual drifts above the estimate, by up
+    to ~2e-11 on the paper-kernel case), and the same solution to 1e-10
+    relative."""
+    w = CASES[name]()
+    h2 = oracle_h2(w)
+    ora = IFMM(h2, w.eps)
+    b, x_o, it_o = _oracle_gmres(w, h2, ora, 1e-13)
     sys = make_sys(ctx, w, tau=ora.tau, rank_cap=1 << 20)
     fac = ifmm.ifmm_factor(ctx, sys)
     try:
         x = torch.empty(w.N, dtype=torch.float64, device="cuda:0")
-        rep = ifmm.gmres_solve(ctx, sys, fac, ifmm.MV_FMM, cuda(b), x, w.N, 1e-10, 500)[0]
-        assert rep.true_rel_residual <= 1e-10
+        rep = ifmm.gmres_solve_ex(ctx, sys, fac, ifmm.MV_FMM, cuda(b), x, w.N, 1e-13, 500,
+                                  refine=0)[0]
+        err = rel(x.cpu().numpy(), x_o)
+        print(f"{name}: GMRES {rep.iters} it (oracle {it_o}), true residual "
+              f"{rep.true_rel_residual:.1e}, |x - x_oracle| / |x_oracle| = {err:.1e}")
+        assert rep.rel_residual <= 1e-13 and rep.true_rel_residual <= 1e-10
         assert abs(rep.iters - it_o) <= 1
-        assert rel(x.cpu().numpy(), x_o) < 1e-8
+        assert err < 1e-10
     finally:
         ifmm.ifmm_factor_destroy(fac)
+        ifmm.ifmm_system_destroy(sys)
+
+
+@pytest.mark.parametrize("name", ["cube2k", "3lev"])
+def test_left_preconditioned_gmres_parity(ctx, name):
+    """Appendix B: the IFMM as left preconditioner on both sides; the stopping
+    criterion is the preconditioned residual.  Same iteration count (+-1), the
+    same solution to 1e-10 at tol 1e-13, and the true residual reported."""
+    w = CASES[name]()
+    h2 = oracle_h2(w)
+    ora = IFMM(h2, w.eps)
+    b, x_o, it_o = _oracle_gmres(w, h2, ora, 1e-13, side="left")
+    sys = make_sys(ctx, w, tau=ora.tau, rank_cap=1 << 20)
+    fac = ifmm.ifmm_factor(ctx, sys)
+    try:
+        x = torch.empty(w.N, dtype=torch.float64, device="cuda:0")
+        rep = ifmm.gmres_solve_ex(ctx, sys, fac, ifmm.MV_FMM, cuda(b), x, w.N, 1e-13, 500,
+                                  side=ifmm.GMRES_LEFT)[0]
+        err = rel(x.cpu().numpy(), x_o)
+        print(f"{name} left: GMRES {rep.iters} it (oracle {it_o}), preconditioned residual "
+              f"{rep.rel_residual:.1e}, true residual {rep.true_rel_residual:.1e}, error {err:.1e}")
+        assert rep.status == 0 and rep.rel_residual <= 1e-13
+        assert abs(rep.iters - it_o) <= 1
+        assert err < 1e-10
+    finally:
+        ifmm.ifmm_factor_destroy(fac)
+        ifmm.ifmm_system_destroy(sys)
+
+
+def test_flexible_gmres_matches_right_gmres(ctx):
+    """Flexible GMRES keeps z_k = M^-1 v_k; with the FP64 preconditioner (one
+    fixed linear map) it spans the same space as right preconditioning: same
+    iterations and the same solution to rounding."""
+    w = CASES["3lev"]()
+    sys = make_sys(ctx, w)
+    fac = ifmm.ifmm_factor(ctx, sys)
+    try:
+        B = cuda(w.rhs(2).T.copy())
+        xr, xf = torch.empty_like(B), torch.empty_like(B)
+        rr = ifmm.gmres_solve(ctx, sys, fac, ifmm.MV_FMM, B, xr, w.N, 1e-10, 300)
+        rf = ifmm.gmres_solve_ex(ctx, sys, fac, ifmm.MV_FMM, B, xf, w.N, 1e-10, 300,
+                                 side=ifmm.GMRES_FLEXIBLE)
+        assert [r.iters for r in rf] == [r.iters for r in rr]
+        assert all(r.status == 0 and r.true_rel_residual <= 1e-10 for r in rf)
+        assert rel(xf.cpu().numpy(), xr.cpu().numpy()) < 1e-8
+    finally:
+        ifmm.ifmm_factor_destroy(fac)
+        ifmm.ifmm_system_destroy(sys)
+
+
+def test_default_path_parity_on_workload_recipe(ctx):
+    """The configuration the benchmark times -- the library's default rank cap
+    (n^D = 64), the randomised SVD of Sec. 2.4 for tall blocks and the symmetric
+    variant -- on the cube-64k recipe itself (1/r, A_ii = 2 N^(1/3), leaves <= 64,
+    Chebyshev 4^3, eps = 1e-8) at N = 8192: three levels, level-2 blocks up to
+    158 rows whose ranks the cap binds.  The randomised threshold is lowered to
+    100 rows on both sides so that it triggers at this size (the library's
+    default, 160, is reached from N ~ 2^15).  Unique results are compared:
+    equal ranks at every depth, and GMRES (non-restarted, tol 1e-13) reaching
+    the oracle's solution within 1e-10 in the same number of iterations (+-1).
+    The preconditioner output itself is not unique here: where the cap binds it
+    cuts through clustered singular values far above tau, and the oracle's own
+    output moves by 2.6e-4 when the points move by 1e-13 (relative) with every
+    rank unchanged; so it is checked for validity -- its normwise backward
+    error against A_n within 1.5x the oracle's, and within 2e-3 of the
+    oracle's output."""
+    from workloads import inv_r_cube
+    w = inv_r_cube(8192, 2000, "cube-64k@8192", 4, 64, 1e-8)
+    h2 = oracle_h2(w)
+    ora = IFMM(h2, w.eps, rank_cap=64, rsvd_rows=100, symmetric=True)
+    assert max(ora.level_a[2]) > 100 and max(ora.level_r[2]) == 64
+    sys = make_sys(ctx, w, tau=ora.tau, rsvd_rows=100, symmetric=1)  # rank_cap 0: default n^D
+    fac = ifmm.ifmm_factor(ctx, sys)
+    try:
+        for l in range(2, h2.tree.L + 1):
+            assert ifmm.ifmm_factor_get_ranks(fac, l) == ora.ranks(l), f"ranks differ at depth {l}"
+        b = w.rhs(1)[:, 0]
+        x = torch.empty(w.N, dtype=torch.float64, device="cuda:0")
+        ifmm.ifmm_solve(ctx, fac, cuda(b), x, w.N)
+        xg, xo = x.cpu().numpy(), ora.solve(b)
+        e_solve = rel(xg, xo)
+        p = h2.tree.perm
+        A = h2.dense_blockwise()
+        from scipy.sparse.linalg import eigsh
+        smax = float(abs(eigsh(A, k=1, which="LM", return_eigenvectors=False)[0]))  # A symmetric
+        eta = lambda v: np.linalg.norm(A @ v[p] - b[p]) / (smax * np.linalg.norm(v))
+        x_o, it_o, _ = oracle_gmres(lambda v: to_user(h2, h2.matvec(v[p])), b, ora.solve,
+                                    1e-13, 500)
+        rep = ifmm.gmres_solve_ex(ctx, sys, fac, ifmm.MV_FMM, cuda(b), x, w.N, 1e-13, 500,
+                                  refine=0)[0]
+        e_gmres = rel(x.cpu().numpy(), x_o)
+        print(f"default path: preconditioner output vs oracle {e_solve:.1e}, backward error "
+              f"{eta(xg):.2e} (oracle {eta(xo):.2e}); GMRES {rep.iters} it (oracle {it_o}), "
+              f"true residual {rep.true_rel_residual:.1e}, vs oracle {e_gmres:.1e}")
+        assert eta(xg) <= 1.5 * eta(xo) and e_solve < 2e-3
+        assert rep.rel_residual <= 1e-13 and abs(rep.iters - it_o) <= 1
+        assert e_gmres < 1e-10
+    finally:
+        ifmm.ifmm_factor_destroy(fac)
+        ifmm.ifmm_system_destroy(sys)
+
+
+def test_square_gauss_shape_parity(ctx):
+    """The square-gauss-1m recipe (points uniform in the unit square, Gaussian
+    sigma = 0.05 with A_ii = 1.01, quadtree leaves <= 128, Chebyshev 6^2,
+    eps = 1e-6) at N = 8192: tree bit-exact, FMM matvec to 1e-13, equal ranks,
+    solve output to 1e-10, and four right-hand sides of GMRES to the oracle's
+    solutions within 1e-10 at tol 1e-13."""
+    from workloads import Kernel as WK
+    w = small_cube(8192, 3000, cheb_n=6, leaf_max=128, eps=1e-6, dim=2,
+                   kernel=WK(K_GAUSSIAN, 0.05, 1.01))
+    h2 = oracle_h2(w)
+    ora = IFMM(h2, w.eps)
+    sys = make_sys(ctx, w, tau=ora.tau, rank_cap=1 << 20)
+    try:
+        assert np.array_equal(ifmm.ifmm_system_get_perm(sys, w.N), h2.tree.perm)
+        X = np.random.default_rng(4).standard_normal((4, w.N))
+        y = torch.empty(4, w.N, dtype=torch.float64, device="cuda:0")
+        ifmm.fmm_matvec(ctx, sys, ifmm.MV_FMM, cuda(X), y, w.N)
+        p = h2.tree.perm
+        ref = np.stack([to_user(h2, h2.matvec(X[c][p])) for c in range(4)])
+        assert rel(y.cpu().numpy(), ref) < 1e-13
+        fac = ifmm.ifmm_factor(ctx, sys)
+        try:
+            for l in range(2, h2.tree.L + 1):
+                assert ifmm.ifmm_factor_get_ranks(fac, l) == ora.ranks(l), f"depth {l}"
+            B = w.rhs(4).T.copy()
+            Xs = torch.empty(4, w.N, dtype=torch.float64, device="cuda:0")
+            ifmm.ifmm_solve(ctx, fac, cuda(B), Xs, w.N)
+            assert rel(Xs.cpu().numpy(), ora.solve(B.T).T) < 1e-10
+            reps = ifmm.gmres_solve_ex(ctx, sys, fac, ifmm.MV_FMM, cuda(B), Xs, w.N, 1e-13, 500,
+                                       refine=0)
+            mv = lambda v: to_user(h2, h2.matvec(v[p]))
+            for c in range(4):
+                x_o, it_o, _ = oracle_gmres(mv, B[c], ora.solve, 1e-13, 500)
+                assert reps[c].rel_residual <= 1e-13 and abs(reps[c].iters - it_o) <= 1
+                assert rel(Xs[c].cpu().numpy(), x_o) < 1e-10, c
+        finally:
+            ifmm.ifmm_factor_destroy(fac)
+    finally:
         ifmm.ifmm_system_destroy(sys)
 
 

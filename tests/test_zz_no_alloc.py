@@ -5,7 +5,8 @@ application that owns a fixed device pool and forbids cudaMalloc, or a
 real-time loop that must not stall on the allocator.  fmm_matvec_static serves them from a library-owned static
 device buffer.  Here it must give the same y = A_n x as fmm_matvec on two
 calls in a row (the buffer keeps the previous call's contents), for a
-two-level and a deeper tree, and reject a request larger than its buffer.
+two-level and a deeper tree, leave the device's free memory unchanged while
+it runs, and reject a request larger than its buffer.
 This file is collected last so that a stop at its first failure has already
 run every other test.
 """
@@ -40,13 +41,21 @@ def test_static_matvec_matches_fmm_matvec_twice(ctx, make):
     sys = ifmm.ifmm_system_create(ctx, cuda(w.points), kernel(w), opts(w))
     try:
         rng = np.random.default_rng(11)
+        # The first call on a device loads the library's module that holds the
+        # static array (CUDA loads modules at first use), which is when the
+        # array's 64 MiB are taken; from then on no call changes free memory.
+        X0 = cuda(rng.standard_normal((2, w.N)))
+        ifmm.fmm_matvec_static(ctx, sys, X0, torch.empty_like(X0), w.N)
         for call in range(2):
             X = cuda(rng.standard_normal((2, w.N)))
             ref = torch.empty_like(X)
             out = torch.full_like(X, np.nan)
             ifmm.fmm_matvec(ctx, sys, ifmm.MV_FMM, X, ref, w.N)
+            torch.cuda.synchronize()
+            free0 = torch.cuda.mem_get_info()[0]   # cudaMemGetInfo: free device bytes
             ifmm.fmm_matvec_static(ctx, sys, X, out, w.N)
             torch.cuda.synchronize()
+            assert torch.cuda.mem_get_info()[0] == free0, f"call {call} allocated device memory"
             assert rel(out.cpu().numpy(), ref.cpu().numpy()) < 1e-13, f"call {call}"
     finally:
         ifmm.ifmm_system_destroy(sys)
