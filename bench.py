@@ -479,14 +479,25 @@ def _serve(args, ifmm, torch, ctx, dev, world, rank, dist, ws, N, n_serve, opt, 
              "window_s": window, "worst_true_rel_residual": worst,
              "gmres_iterations_p50": _pct([d[5] for d in done], 50),
              "gmres_iterations_max": max((d[5] for d in done), default=None)}
-    # per-kernel profile of one more window (not timed: the event pairs cost time)
+    # per-kernel profile (not timed: the event pairs cost time, and kernels of
+    # concurrent workers would stretch each other's intervals): one 32-column
+    # block of the largest admitted system, alone on one stream, through the
+    # same flexible GMRES with FP32 sweeps the server runs
+    big = max(admitted, key=lambda s_: N[s_])
+    Bp = pools_d[big]
+    Xp = torch.empty_like(Bp)
+    ifmm.gmres_solve_ex(ctx, systems[big], facs[big], ifmm.MV_FMM, Bp, Xp, N[big], 1e-10,
+                        SERVE_MAXIT, side=ifmm.GMRES_FLEXIBLE, precond_precision=ifmm.P_FP32)
+    torch.cuda.synchronize()
     ifmm.ifmm_profile_start(ctx)
-    load.done.clear()
     t0 = time.perf_counter()
-    load.run(args.step_seconds * 2)
-    load.drain()
+    preps = ifmm.gmres_solve_ex(ctx, systems[big], facs[big], ifmm.MV_FMM, Bp, Xp, N[big], 1e-10,
+                                SERVE_MAXIT, side=ifmm.GMRES_FLEXIBLE,
+                                precond_precision=ifmm.P_FP32)
     stats = ifmm.ifmm_profile_stop(ctx)
     prof_s = time.perf_counter() - t0
+    serve["profiled_block"] = {"system_N": N[big], "columns": 32, "seconds": prof_s,
+                               "gmres_iterations_max": max(r.iters for r in preps)}
     # end to end: host-buffer requests through ifmm_server_submit
     e2e = None
     if not args.no_e2e:

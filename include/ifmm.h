@@ -44,7 +44,7 @@ typedef enum {
   IFMM_ERR_NOT_CONVERGED = 5,  /* GMRES reached maxit above tol (report still filled) */
   IFMM_ERR_TIMEOUT = 6,        /* a bounded device wait ran out, or ifmm_server_wait's limit */
   IFMM_ERR_BUDGET = 7,         /* server admission refused, or a request shed              */
-  IFMM_ERR_UNSUPPORTED = 8     /* e.g. BF16 Schur products (declared, not implemented)     */
+  IFMM_ERR_UNSUPPORTED = 8     /* e.g. a rank query on a system without a tree             */
 } ifmm_status;
 
 /* Kernel of the matrix (Sec. 3.1). */
@@ -65,9 +65,10 @@ typedef struct {
  * elimination (Sec. 2.2, Algorithm 2).  FP64: FP64 FMA.  TF32: operands rounded
  * to TF32 on the tcgen05 tensor cores, FP32 accumulation.  FP32: each operand
  * split into two TF32 parts, three tensor-core products (hi*hi + hi*lo + lo*hi),
- * FP32 accumulation -- close to FP32 accuracy.  The pivot LU, the solve for
- * E(P,P)^-1 E(P,C), every SVD and rank decision, the solve sweeps and GMRES
- * stay in FP64.  BF16 is declared but not implemented (IFMM_ERR_UNSUPPORTED). */
+ * FP32 accumulation -- close to FP32 accuracy.  BF16: operands rounded to BF16
+ * (8 significant bits), FP32 accumulation; allowed only with eps >= 1e-4
+ * (IFMM_ERR_INVALID_ARG otherwise).  The pivot LU, the solve for
+ * E(P,P)^-1 E(P,C), every SVD and rank decision and GMRES stay in FP64. */
 typedef enum { IFMM_P_FP64 = 0, IFMM_P_TF32 = 1, IFMM_P_BF16 = 2, IFMM_P_FP32 = 3 } ifmm_precision;
 
 typedef struct {
@@ -342,9 +343,10 @@ const char* ifmm_server_last_error(ifmm_server* srv);
 
 /* ---- Schur product kernel ----------------------------------------------------- */
 /* C = alpha op(A) op(B) + beta C with the kernel the elimination uses for its
- * Schur products at precision `prec` (ifmm_precision; FP64, TF32 or FP32) --
+ * Schur products at precision `prec` (ifmm_precision) --
  * the trailing update of Sec. 2.2, exposed so that a caller can check or time
- * it on its own matrices.  A, B, C: device, FP64, column-major; op(A) is M x K
+ * it on its own matrices (prec: FP64, TF32, FP32 or BF16).  A, B, C: device,
+ * FP64, column-major; op(A) is M x K
  * (A is M x K with lda >= M, or K x M with lda >= K when transA), op(B) is
  * K x N likewise, C is M x N with ldc >= M and must not overlap A or B.
  * beta == 0 does not read C.  IFMM_ERR_TIMEOUT if a tensor-core wait ran out

@@ -279,8 +279,8 @@ ifmm_status ifmm_schur_product(ifmm_ctx* ctx, int prec, int M, int N, int K, con
                                int lda, int transA, const double* B, int ldb, int transB,
                                double* C, int ldc, double alpha, double beta, ifmm_stream stream) {
   if (!ctx || M < 0 || N < 0 || K < 0 || !C) return IFMM_ERR_INVALID_ARG;
-  if (prec != IFMM_P_FP64 && prec != IFMM_P_TF32 && prec != IFMM_P_FP32)
-    return prec == IFMM_P_BF16 ? IFMM_ERR_UNSUPPORTED : IFMM_ERR_INVALID_ARG;
+  if (prec != IFMM_P_FP64 && prec != IFMM_P_TF32 && prec != IFMM_P_FP32 && prec != IFMM_P_BF16)
+    return IFMM_ERR_INVALID_ARG;
   if (K > 0 && (!A || !B)) return IFMM_ERR_INVALID_ARG;
   if (ldc < std::max(M, 1) || lda < std::max(transA ? K : M, 1) ||
       ldb < std::max(transB ? N : K, 1))
@@ -298,7 +298,7 @@ ifmm_status ifmm_schur_product(ifmm_ctx* ctx, int prec, int M, int N, int K, con
     CK(cudaMemsetAsync(err, 0, sizeof(int), s));
     const GemmTask t{A, B, C, lda, ldb, ldc, M, N, K, transA ? 1 : 0, transB ? 1 : 0, alpha, beta};
     if (prec == IFMM_P_FP64) run_gemms(ar, {t}, s);
-    else run_gemms_tc(ar, {t}, prec == IFMM_P_FP32, err, s);
+    else run_gemms_tc(ar, {t}, prec, err, s);
     int h = 0;
     CK(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));

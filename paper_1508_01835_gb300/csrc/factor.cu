@@ -569,8 +569,8 @@ struct Factorizer {
     // Schur products S = E(R,P) G: FP64, or the tensor cores in the
     // mixed-precision modes (a wait that runs out counts in d_counters[1])
     const int prec = sys->opt.schur;
-    if (prec == IFMM_P_TF32 || prec == IFMM_P_FP32)
-      run_gemms_tc(scratch, gs, prec == IFMM_P_FP32, d_counters + 1, s);
+    if (prec == IFMM_P_TF32 || prec == IFMM_P_FP32 || prec == IFMM_P_BF16)
+      run_gemms_tc(scratch, gs, prec, d_counters + 1, s);
     else
       run_gemms(scratch, gs, s);
     if (checking()) {

@@ -259,13 +259,11 @@ void launch_gemm(const GemmTask* d_tasks, const GemmTile* d_tiles, int ntiles, c
 void run_gemms(Arena& ar, const std::vector<GemmTask>& tasks, cudaStream_t s);
 
 // Tensor-core form of run_gemms for the Schur products (kernels_tc.cu):
-// 128 x 128 output tiles, operands rounded to TF32 (split: head + tail, the
-// three-term compensated product), FP32 accumulation in tensor memory, FP64
-// epilogue.  *d_err is set to 1 if a bounded wait ran out.
-void gemm_tc_tiles(const GemmTask& t, int task_index, std::vector<GemmTile>& tiles);
-void launch_gemm_tc(const GemmTask* d_tasks, const GemmTile* d_tiles, int ntiles, bool split,
-                    int* d_err, cudaStream_t s, double flops = 0.0);
-void run_gemms_tc(Arena& ar, const std::vector<GemmTask>& tasks, bool split, int* d_err,
+// operands packed once (TF32, TF32 head + tail for the three-term compensated
+// product, or BF16; prec = IFMM_P_TF32 / IFMM_P_FP32 / IFMM_P_BF16), 128 x 128
+// output tiles of a persistent pipelined kernel, FP32 accumulation in tensor
+// memory, FP64 epilogue.  *d_err is set to 1 if a bounded wait ran out.
+void run_gemms_tc(Arena& ar, const std::vector<GemmTask>& tasks, int prec, int* d_err,
                   cudaStream_t s);
 
 // Edge redirection of Algorithm 3 (kernels_edges.cu), one CTA per

@@ -3,43 +3,49 @@
 //
 // The trailing update of an eliminated box, E(R,C) -= E(R,P) E(P,P)^-1 E(P,C)
 // (Sec. 2.2, Algorithm 2), is the one dense contraction of the factorisation.
-// In the mixed-precision mode its product S = E(R,P) G runs here:
-//   * operands are FP64 in global memory; each CTA rounds a 128 x 32 slice of
-//     A and of B to TF32 (round to nearest, with integer arithmetic: the FP64
-//     unit is the scarce one) and stores them in shared memory in the tensor
-//     core's K-major, unswizzled core-matrix layout;
-//   * IFMM_P_FP32 splits every operand into a TF32 head and a TF32 tail
-//     (x = hi + lo) and accumulates hi*hi + hi*lo + lo*hi -- the three-term
-//     error-compensated TF32 product of Ootomo and Yokota (2022), close to
-//     FP32 accuracy; IFMM_P_TF32 accumulates hi*hi only;
-//   * one elected thread issues tcgen05.mma (kind::tf32, M = 128, N = 128,
-//     K = 8 per instruction) into an FP32 accumulator in tensor memory and
-//     commits each stage to an mbarrier; two stages let the next slice load
-//     while the tensor core works on the previous one;
-//   * the epilogue reads the accumulator with tcgen05.ld (warp w owns lanes
-//     32w .. 32w + 31, i.e. output rows) and writes C = beta C + alpha S in FP64.
+// In the mixed-precision modes its product S = E(R,P) G runs here, in two
+// passes:
+//   1. packing: every operand (FP64 in global memory) is rounded once --
+//      TF32 head and tail (x = hi + lo, IFMM_P_FP32: the three-term
+//      error-compensated product of Ootomo and Yokota, 2022), TF32 head only
+//      (IFMM_P_TF32), or BF16 (IFMM_P_BF16) -- with integer arithmetic (the
+//      FP64 unit is the scarce one) and written in the tensor core's K-major,
+//      unswizzled core-matrix layout: one 16 KB block per 128 rows and K slice
+//      (32 TF32 or 64 BF16 values), zero-padded, ready to be copied verbatim;
+//   2. the product: a persistent kernel, one CTA per SM looping over 128 x 128
+//      output tiles, with warp roles: warp 0 streams each K slice's blocks into
+//      a ring of shared-memory stages with bulk asynchronous copies (the TMA
+//      engine's cp.async.bulk, completion counted in bytes on an mbarrier);
+//      warp 1's elected thread issues tcgen05.mma (K = 8 per instruction for
+//      TF32, 16 for BF16) into one of two FP32 accumulators in tensor memory
+//      and commits each stage back to the producer; warps 2-5 read a finished
+//      accumulator with tcgen05.ld (each warp its quarter of the 128 lanes =
+//      output rows), write C = beta C + alpha S in FP64 and hand the
+//      accumulator back, so the epilogue of one tile overlaps the MMAs of the
+//      next.
 // The pivot LU, the solve for G and every rank decision stay in FP64.
 //
-// Every wait on an mbarrier is bounded; a wait that runs out records an error
-// code in *err and the CTA still drains its own tensor-core work (again with a
-// bound) and frees its tensor memory before it returns.  A pipeline wait that
-// takes more than `soft_polls` polls is also recorded in *err (the caller
-// reports IFMM_ERR_TIMEOUT) but keeps waiting up to the hard bound; the soft
-// limit equals the hard one unless IFMM_TC_SOFT_WAIT_POLLS lowers it (then the
-// first polls are non-blocking test_wait), which is how a test makes a wait run
-// out without leaving any work in flight.
+// Every wait on an mbarrier is bounded.  A wait that runs out records an
+// error code in *err and its role stops; the MMA thread's last commit is
+// waited for (again bounded) before the tensor memory is freed, so no MMA is
+// in flight when it is.  A pipeline wait that takes more than `soft_polls`
+// non-blocking polls is also recorded in *err (the caller reports
+// IFMM_ERR_TIMEOUT) but keeps waiting up to the hard bound; the soft limit
+// equals the hard one unless IFMM_TC_SOFT_WAIT_POLLS lowers it, which is how a
+// test makes a wait run out without leaving any work in flight.
 #include "internal.cuh"
 
 namespace ifmm {
 
 namespace tc {
 
-constexpr int BM = 128, BN = 128, BK = 32;  // output tile and K slice per stage
-constexpr int NTHREADS = 128;
-constexpr int TMEM_COLS = 128;              // FP32 accumulator: 128 lanes x 128 columns
-// one operand slice: 128 rows x 32 TF32 values = 16 KB
-constexpr int SLICE_BYTES = BM * BK * 4;
+constexpr int BM = 128, BN = 128;            // output tile
+constexpr int BLOCK_BYTES = 16384;           // one packed operand block: 128 rows x 128 bytes of K
+constexpr int NTHREADS = 192;                // warp 0 producer, warp 1 MMA, warps 2-5 epilogue
+constexpr int TMEM_COLS = 256;               // two FP32 accumulators of 128 columns
+constexpr int STAGE_BUDGET = 3 * 65536;      // shared-memory ring
 constexpr long long SPIN_LIMIT = 1ll << 22;  // bounded waits (far above any legal wait)
+constexpr int MODE_TF32 = 0, MODE_SPLIT = 1, MODE_BF16 = 2;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -56,19 +62,6 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
   d |= (uint64_t)((sbo & 0x3FFFF) >> 4) << 32;
   d |= (uint64_t)1 << 46;
   return d;  // base offset 0, absolute LBO mode off, layout type 0 (no swizzle)
-}
-
-// Instruction descriptor of kind::tf32: D = F32, A = B = TF32, both K-major,
-// N >> 3 in bits 17-22, M >> 4 in bits 24-28.
-constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                           ((uint32_t)(BM >> 4) << 24);
-
-__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
-      "l"(a), "l"(b), "r"(IDESC), "r"(acc));
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -217,167 +210,294 @@ __device__ __forceinline__ double widen(float f) {
   return __longlong_as_double((long long)(sgn | (de << 52) | mant));
 }
 
-// Byte offset of element (row, k) of a 128 x 32 K-major slice: core matrix
-// (row / 8, k / 4) at ((k / 4) * 16 + row / 8) * 128, inside it row % 8 at
-// 16-byte stride and k % 4 at 4-byte stride.  Hence sbo = 128 (next 8 rows)
-// and lbo = 2048 (next 4 values of k).
-constexpr uint32_t SBO = 128, LBO = (BM / 8) * 128;
-__device__ __forceinline__ uint32_t slice_off(int row, int kq) {  // kq = k / 4
-  return (uint32_t)((kq * (BM / 8) + (row >> 3)) * 128 + (row & 7) * 16);
+
+// Instruction descriptors: D = F32, A and B K-major, N >> 3 in bits 17-22,
+// M >> 4 in bits 24-28; kind::tf32 with A = B = TF32 (format 2), kind::f16
+// with A = B = BF16 (format 1).
+constexpr uint32_t IDESC_TF32 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                ((uint32_t)(BM >> 4) << 24);
+constexpr uint32_t IDESC_BF16 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(IDESC_TF32), "r"(acc));
+}
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(IDESC_BF16), "r"(acc));
 }
 
-// Load op(X)[row0 + r, k0 + k] for r < 128, k < 32 (zero outside rows x K),
-// rounded to TF32 (head; tail = TF32 of the remainder when `split`).
-// op(X)[m, k] = X[m + k ld] (trans == 0) or X[k + m ld] (trans == 1).
-__device__ __forceinline__ void load_slice(const double* __restrict__ X, int ld, int trans,
-                                           int rows, int K, int row0, int k0, char* hi, char* lo,
-                                           bool split) {
-  // 128 rows x 8 groups of 4 values; thread t takes row t % 128 for trans == 0
-  // (consecutive threads read consecutive rows: coalesced) and the 4 values of
-  // one k-group (contiguous for trans == 1).
-  for (int e = threadIdx.x; e < BM * (BK / 4); e += NTHREADS) {
-    const int r = e % BM, kq = e / BM;
-    const int gr = row0 + r;
-    float4 h, l;
-    float hv[4], lv[4];
-#pragma unroll
-    for (int j = 0; j < 4; j++) {
-      const int gk = k0 + kq * 4 + j;
-      double v = 0.0;
-      if (gr < rows && gk < K) v = trans ? X[gk + (long long)gr * ld] : X[gr + (long long)gk * ld];
-      split_tf32(v, hv[j], lv[j]);
-      if (!split) lv[j] = 0.0f;
-    }
-    h = make_float4(hv[0], hv[1], hv[2], hv[3]);
-    l = make_float4(lv[0], lv[1], lv[2], lv[3]);
-    const uint32_t off = slice_off(r, kq);
-    *reinterpret_cast<float4*>(hi + off) = h;
-    if (split) *reinterpret_cast<float4*>(lo + off) = l;
-  }
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// bulk asynchronous copy global -> shared (TMA engine, non-tensor form);
+// completion is counted in bytes on `bar`
+__device__ __forceinline__ void bulk_copy(void* dst_smem, const void* src, uint32_t bytes,
+                                          uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst_smem)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// v rounded to BF16 (8 significant bits, nearest, halves away from zero) as
+// a 16-bit pattern, with integer arithmetic; |v| < 2^-100 flushes to zero,
+// overflow becomes infinity.
+__device__ __forceinline__ unsigned short round_bf16(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned int sgn = (unsigned int)(b >> 63) << 15;
+  const int e = (int)((b >> 52) & 0x7FF);
+  if (e < 1023 - 100) return (unsigned short)sgn;
+  const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  unsigned long long mh = (m + (1ull << 44)) >> 45;  // 8 significant bits, or 2^8
+  int eh = e;
+  if (mh >> 8) { mh >>= 1; eh += 1; }
+  const int fe = eh - 1023 + 127;
+  if (fe >= 255) return (unsigned short)(sgn | 0x7F80u);
+  return (unsigned short)(sgn | ((unsigned int)fe << 7) | (unsigned int)(mh & 0x7F));
+}
+
+// Byte offset of element (row, k) inside a packed 16 KB block: core matrix
+// (row / 8, k-group) at (kgroup * 16 + row / 8) * 128 and row % 8 at 16-byte
+// stride inside it, where a k-group is 16 bytes of K (4 TF32 or 8 BF16
+// values).  Hence the descriptors' sbo = 128 (next 8 rows) and lbo = 2048
+// (next 16 bytes of K); one MMA (32 bytes of K) spans two k-groups.
+constexpr uint32_t SBO = 128, LBO = (BM / 8) * 128;
+__device__ __forceinline__ uint32_t block_off(int row, int kgroup) {
+  return (uint32_t)((kgroup * (BM / 8) + (row >> 3)) * 128 + (row & 7) * 16);
 }
 
 }  // namespace tc
 
-// One 128 x 128 output tile per CTA.  Shared memory: 2 stages x {A hi, B hi,
-// A lo, B lo} slices (the lo slices only in split mode) + barriers.
-__global__ void __launch_bounds__(tc::NTHREADS) k_gemm_tc(const GemmTask* __restrict__ tasks,
-                                                          const GemmTile* __restrict__ tiles,
-                                                          int split, int* __restrict__ err,
-                                                          long long soft_polls) {
+// ---------------------------------------------------------------------------
+// Pass 1: packing.  One CTA per (operand, row block, K slice) writes the
+// block(s) of 128 rows x one K slice of op(X) (rows / K beyond the matrix are
+// zero).  op(X)[r, k] = X[r + k ld] (trans == 0) or X[k + r ld] (trans == 1).
+// ---------------------------------------------------------------------------
+struct TcPack {
+  const double* X;
+  long long ld;
+  int trans, rows, K;
+  int rb, ks;          // row block and K slice of this CTA
+  char* hi;            // destination block (16 KB)
+  char* lo;            // tail block (split mode) or nullptr
+};
+
+__global__ void __launch_bounds__(128) k_tc_pack(const TcPack* __restrict__ packs, int mode) {
+  using namespace tc;
+  const TcPack P = packs[blockIdx.x];
+  const int kslice = mode == MODE_BF16 ? 64 : 32;
+  const int per = mode == MODE_BF16 ? 8 : 4;  // values per 16-byte k-group
+  const int ngroups = kslice / per;           // 8
+  for (int e = threadIdx.x; e < BM * ngroups; e += blockDim.x) {
+    const int r = e % BM, g = e / BM;  // consecutive threads: consecutive rows
+    const int gr = P.rb * BM + r;
+    const uint32_t off = block_off(r, g);
+    if (mode == MODE_BF16) {
+      unsigned int w[4];
+#pragma unroll
+      for (int j = 0; j < 8; j += 2) {
+        unsigned short h2[2];
+#pragma unroll
+        for (int q = 0; q < 2; q++) {
+          const int gk = P.ks * kslice + g * per + j + q;
+          double v = 0.0;
+          if (gr < P.rows && gk < P.K) v = P.trans ? P.X[gk + (long long)gr * P.ld] : P.X[gr + (long long)gk * P.ld];
+          h2[q] = round_bf16(v);
+        }
+        w[j / 2] = (unsigned int)h2[0] | ((unsigned int)h2[1] << 16);
+      }
+      *reinterpret_cast<uint4*>(P.hi + off) = make_uint4(w[0], w[1], w[2], w[3]);
+    } else {
+      float hv[4], lv[4];
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        const int gk = P.ks * kslice + g * per + j;
+        double v = 0.0;
+        if (gr < P.rows && gk < P.K) v = P.trans ? P.X[gk + (long long)gr * P.ld] : P.X[gr + (long long)gk * P.ld];
+        split_tf32(v, hv[j], lv[j]);
+      }
+      *reinterpret_cast<float4*>(P.hi + off) = make_float4(hv[0], hv[1], hv[2], hv[3]);
+      if (P.lo) *reinterpret_cast<float4*>(P.lo + off) = make_float4(lv[0], lv[1], lv[2], lv[3]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Pass 2: the persistent product kernel.
+// ---------------------------------------------------------------------------
+struct TcTask {
+  const char* A;   // packed A: block (rb, ks) at ((rb * nks + ks) * planes + plane) * 16 KB
+  const char* B;   // packed op(B) (N rows), same arrangement
+  double* C;
+  int ldc, M, N, nks;
+  double alpha, beta;
+};
+struct TcTile {
+  int task, rb, nb;
+};
+
+__global__ void __launch_bounds__(tc::NTHREADS, 1)
+    k_gemm_tc(const TcTask* __restrict__ tasks, const TcTile* __restrict__ tiles, int ntiles,
+              int mode, int* __restrict__ err, long long soft_polls) {
   using namespace tc;
   extern __shared__ __align__(1024) char smem_raw[];
-  // 1024-byte alignment of the operand area
   char* smem = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const int nsl = split ? 4 : 2;  // slices per stage
-  char* stage[2] = {smem, smem + nsl * SLICE_BYTES};
-  __shared__ uint64_t bar[2];
+  const int planes = mode == MODE_SPLIT ? 2 : 1;
+  const int stage_bytes = 2 * planes * BLOCK_BYTES;  // A and B blocks of one K slice
+  const int nst = STAGE_BUDGET / stage_bytes;         // 3 (split) or 6 stages
+  __shared__ uint64_t full[6], empty[6], accf[2], acce[2], done;
   __shared__ uint32_t tmem_base_s;
-  const GemmTile tl = tiles[blockIdx.x];
-  const GemmTask t = tasks[tl.task];
+  __shared__ int abort_sh;
+  volatile int& abort_s = abort_sh;  // read in loops: never cached in a register
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-  if (warp == 0) {
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < nst; s++) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; a++) {
+      mbar_init(&accf[a], 1);
+      mbar_init(&acce[a], 128);
+    }
+    mbar_init(&done, 1);
+    abort_s = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tmem_base_s)),
                  "r"(TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  if (threadIdx.x == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
   fence_before();
   __syncthreads();
   fence_after();
   const uint32_t tmem = tmem_base_s;
+  bool late = false;
 
-  const int nk = (t.K + BK - 1) / BK;
-  bool ok = true, late = false;
-  for (int kt = 0; kt < nk; kt++) {
-    const int s = kt & 1;
-    if (kt >= 2) {
-      // the MMAs that read this stage two slices ago must be done
-      if (!mbar_wait_soft(&bar[s], (uint32_t)(((kt - 2) >> 1) & 1), soft_polls, &late)) ok = false;
-    }
-    char* st = stage[s];
-    load_slice(t.A, t.lda, t.transA, t.M, t.K, tl.m0, kt * BK, st, split ? st + 2 * SLICE_BYTES : nullptr,
-               split != 0);
-    load_slice(t.B, t.ldb, !t.transB, t.N, t.K, tl.n0, kt * BK, st + SLICE_BYTES,
-               split ? st + 3 * SLICE_BYTES : nullptr, split != 0);
-    fence_async_smem();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      fence_after();
-      const uint32_t a_hi = smem_u32(st), b_hi = smem_u32(st + SLICE_BYTES);
-      const uint32_t a_lo = smem_u32(st + 2 * SLICE_BYTES), b_lo = smem_u32(st + 3 * SLICE_BYTES);
-#pragma unroll
-      for (int kk = 0; kk < BK / 8; kk++) {
-        const uint32_t o = kk * 2 * LBO;  // 8 values of k = two core matrices
-        const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
-        if (split) {
-          mma_tf32(tmem, smem_desc(a_lo + o, LBO, SBO), smem_desc(b_hi + o, LBO, SBO), acc);
-          mma_tf32(tmem, smem_desc(a_hi + o, LBO, SBO), smem_desc(b_lo + o, LBO, SBO), 1u);
-          mma_tf32(tmem, smem_desc(a_hi + o, LBO, SBO), smem_desc(b_hi + o, LBO, SBO), 1u);
-        } else {
-          mma_tf32(tmem, smem_desc(a_hi + o, LBO, SBO), smem_desc(b_hi + o, LBO, SBO), acc);
+  if (warp == 0) {
+    // ---- producer: stream the K slices of every tile into the ring ----
+    if (lane == 0) {
+      int st = 0;
+      uint32_t ph = 0;
+      for (int t = blockIdx.x; t < ntiles && !abort_s; t += gridDim.x) {
+        const TcTile tl = tiles[t];
+        const TcTask T = tasks[tl.task];
+        for (int ks = 0; ks < T.nks; ks++) {
+          if (!mbar_wait_soft(&empty[st], ph ^ 1u, soft_polls, &late)) { abort_s = 1; break; }
+          char* sa = smem + st * stage_bytes;
+          char* sb = sa + planes * BLOCK_BYTES;
+          const char* ga = T.A + ((size_t)tl.rb * T.nks + ks) * planes * BLOCK_BYTES;
+          const char* gb = T.B + ((size_t)tl.nb * T.nks + ks) * planes * BLOCK_BYTES;
+          mbar_expect_tx(&full[st], (uint32_t)stage_bytes);
+          bulk_copy(sa, ga, planes * BLOCK_BYTES, &full[st]);
+          bulk_copy(sb, gb, planes * BLOCK_BYTES, &full[st]);
+          if (++st == nst) { st = 0; ph ^= 1u; }
         }
       }
-      mma_commit(&bar[s]);
     }
-  }
-  // wait for the last commit of each stage (every thread, so all see the result)
-  for (int s = 0; s < 2; s++) {
-    const int n_s = (nk - s + 1) / 2;  // commits on stage s
-    if (n_s > 0 && !mbar_wait_soft(&bar[s], (uint32_t)((n_s - 1) & 1), soft_polls, &late)) ok = false;
-  }
-  if (late) atomicExch(err, 1);  // results are complete; the lateness is reported
-  // one verdict for the whole CTA: the epilogue's tcgen05.ld is warp-collective
-  ok = __syncthreads_and(ok) != 0;
-  fence_after();
-  if (ok && nk > 0) {
-    const int row = tl.m0 + warp * 32 + lane;
-    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
-    for (int c0 = 0; c0 < BN; c0 += 32) {
-      if (tl.n0 + c0 >= t.N) break;  // warp-uniform
-      float v[32];
-      tc::tmem_ld32(lane_addr + c0, v);
-      if (row < t.M) {
-        const bool plain = (t.alpha == 1.0 && t.beta == 0.0);  // the Schur product: C = S
+  } else if (warp == 1) {
+    // ---- MMA issuer ----
+    if (lane == 0) {
+      int st = 0, acc = 0;
+      uint32_t ph = 0, aph = 0;
+      for (int t = blockIdx.x; t < ntiles && !abort_s; t += gridDim.x) {
+        const TcTask T = tasks[tiles[t].task];
+        if (!mbar_wait_soft(&acce[acc], aph ^ 1u, soft_polls, &late)) { abort_s = 1; break; }
+        fence_after();
+        const uint32_t d = tmem + (uint32_t)(acc * BN);
+        for (int ks = 0; ks < T.nks; ks++) {
+          if (!mbar_wait_soft(&full[st], ph, soft_polls, &late)) { abort_s = 1; break; }
+          fence_after();
+          const uint32_t a_hi = smem_u32(smem + st * stage_bytes);
+          const uint32_t a_lo = a_hi + BLOCK_BYTES;
+          const uint32_t b_hi = a_hi + planes * BLOCK_BYTES;
+          const uint32_t b_lo = b_hi + BLOCK_BYTES;
 #pragma unroll
-        for (int j = 0; j < 32; j++) {
-          const int col = tl.n0 + c0 + j;
-          if (col < t.N) {
-            double* c = t.C + row + (long long)col * t.ldc;
-            const double s = widen(v[j]);
-            *c = plain ? s : ((t.beta == 0.0) ? t.alpha * s : t.beta * (*c) + t.alpha * s);
+          for (int kk = 0; kk < 4; kk++) {
+            const uint32_t o = kk * 2 * LBO;  // 32 bytes of K = two k-groups
+            const uint32_t first = (ks > 0 || kk > 0) ? 1u : 0u;
+            if (mode == MODE_SPLIT) {
+              mma_tf32(d, smem_desc(a_lo + o, LBO, SBO), smem_desc(b_hi + o, LBO, SBO), first);
+              mma_tf32(d, smem_desc(a_hi + o, LBO, SBO), smem_desc(b_lo + o, LBO, SBO), 1u);
+              mma_tf32(d, smem_desc(a_hi + o, LBO, SBO), smem_desc(b_hi + o, LBO, SBO), 1u);
+            } else if (mode == MODE_TF32) {
+              mma_tf32(d, smem_desc(a_hi + o, LBO, SBO), smem_desc(b_hi + o, LBO, SBO), first);
+            } else {
+              mma_bf16(d, smem_desc(a_hi + o, LBO, SBO), smem_desc(b_hi + o, LBO, SBO), first);
+            }
+          }
+          mma_commit(&empty[st]);  // the stage is free once these MMAs have read it
+          if (++st == nst) { st = 0; ph ^= 1u; }
+        }
+        mma_commit(&accf[acc]);  // the accumulator is complete
+        if (++acc == 2) { acc = 0; aph ^= 1u; }
+      }
+      mma_commit(&done);  // completes when every MMA issued above has
+    }
+  } else {
+    // ---- epilogue: warps 2..5, TMEM lane quarter = warp % 4 ----
+    const int q = warp & 3;
+    const int rl = q * 32 + lane;  // row inside the tile
+    int acc = 0;
+    uint32_t aph = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      const TcTile tl = tiles[t];
+      const TcTask T = tasks[tl.task];
+      bool ok = mbar_wait_soft(&accf[acc], aph, soft_polls, &late);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok || abort_s) { abort_s = 1; break; }
+      fence_after();
+      const int row = tl.rb * BM + rl;
+      const uint32_t lane_addr = tmem + (uint32_t)(acc * BN) + ((uint32_t)(q * 32) << 16);
+      const bool plain = (T.alpha == 1.0 && T.beta == 0.0);  // the Schur product: C = S
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        if (tl.nb * BN + c0 >= T.N) break;  // warp-uniform
+        float v[32];
+        tmem_ld32(lane_addr + c0, v);
+        if (row < T.M) {
+#pragma unroll
+          for (int j = 0; j < 32; j++) {
+            const int col = tl.nb * BN + c0 + j;
+            if (col < T.N) {
+              double* c = T.C + row + (long long)col * T.ldc;
+              const double s = widen(v[j]);
+              *c = plain ? s : ((T.beta == 0.0) ? T.alpha * s : T.beta * (*c) + T.alpha * s);
+            }
           }
         }
       }
-    }
-  } else if (nk == 0) {
-    // K == 0: C = beta C
-    for (int e = threadIdx.x; e < BM * BN; e += NTHREADS) {
-      const int r = tl.m0 + e % BM, c = tl.n0 + e / BM;
-      if (r < t.M && c < t.N) {
-        double* p = t.C + r + (long long)c * t.ldc;
-        *p = (t.beta == 0.0) ? 0.0 : t.beta * (*p);
-      }
+      fence_before();
+      mbar_arrive(&acce[acc]);  // hand the accumulator back
+      if (++acc == 2) { acc = 0; aph ^= 1u; }
     }
   }
-  if (!ok) {
-    // a wait ran out: record it, then give the committed work one more bounded
-    // chance to finish before the accumulator's tensor memory is freed
-    if (threadIdx.x == 0) atomicExch(err, 1);
-    for (int s = 0; s < 2; s++) {
-      const int n_s = (nk - s + 1) / 2;
-      if (n_s > 0) mbar_wait(&bar[s], (uint32_t)((n_s - 1) & 1));
-    }
-  }
+  // every thread waits for the MMA thread's last commit (so no MMA is in
+  // flight), then warp 1 frees the tensor memory
+  __syncthreads();
+  if (!mbar_wait(&done, 0u)) abort_s = 1;
+  __syncthreads();
+  if (threadIdx.x == 0 && (late || abort_s)) atomicExch(err, 1);
+  if (late && threadIdx.x != 0) atomicExch(err, 1);
   fence_before();
   __syncthreads();
-  if (warp == 0) {
+  if (warp == 1) {
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(TMEM_COLS)
@@ -385,49 +505,70 @@ __global__ void __launch_bounds__(tc::NTHREADS) k_gemm_tc(const GemmTask* __rest
   }
 }
 
-// Two stages of slices, 1 KB for alignment, and 48 KB of slack past the last
-// slice so that no descriptor walk can leave the CTA's allocation.
-size_t gemm_tc_smem(bool split) {
-  return (size_t)2 * (split ? 4 : 2) * tc::SLICE_BYTES + 1024 + 48 * 1024;
-}
+// Ring of stages (3 x 64 KB), 1 KB for alignment and 16 KB of slack past the
+// last stage so that no descriptor walk can leave the CTA's allocation.
+static size_t gemm_tc_smem() { return (size_t)tc::STAGE_BUDGET + 1024 + 16 * 1024; }
 
-void gemm_tc_tiles(const GemmTask& t, int ti, std::vector<GemmTile>& tiles) {
-  if (t.M <= 0 || t.N <= 0) return;
-  for (int n0 = 0; n0 < t.N; n0 += tc::BN)
-    for (int m0 = 0; m0 < t.M; m0 += tc::BM) tiles.push_back({ti, m0, n0});
-}
-
-void launch_gemm_tc(const GemmTask* d_tasks, const GemmTile* d_tiles, int ntiles, bool split,
-                    int* d_err, cudaStream_t s, double flops) {
-  if (ntiles <= 0) return;
-  set_max_dynamic_smem((const void*)k_gemm_tc, (int)gemm_tc_smem(true));
-  Prof p(split ? "k_gemm_tc_3xtf32" : "k_gemm_tc_tf32", flops, 0.0, s);
-  // test hook: a lower reporting limit for the pipeline waits (see k_gemm_tc)
-  long long soft = tc::SPIN_LIMIT;
-  if (const char* e = std::getenv("IFMM_TC_SOFT_WAIT_POLLS")) {
-    const long long v = std::atoll(e);
-    if (v >= 1) soft = std::min(v, tc::SPIN_LIMIT);
-  }
-  k_gemm_tc<<<ntiles, tc::NTHREADS, gemm_tc_smem(split), s>>>(d_tasks, d_tiles, split ? 1 : 0,
-                                                             d_err, soft);
-  CK_LAUNCH("k_gemm_tc");
-}
-
-void run_gemms_tc(Arena& ar, const std::vector<GemmTask>& tasks, bool split, int* d_err,
+void run_gemms_tc(Arena& ar, const std::vector<GemmTask>& tasks, int prec, int* d_err,
                   cudaStream_t s) {
-  std::vector<GemmTask> kept;
-  std::vector<GemmTile> tiles;
+  using namespace tc;
+  const int mode = prec == IFMM_P_FP32 ? MODE_SPLIT : (prec == IFMM_P_BF16 ? MODE_BF16 : MODE_TF32);
+  const int planes = mode == MODE_SPLIT ? 2 : 1;
+  const int kslice = mode == MODE_BF16 ? 64 : 32;
+  std::vector<TcPack> packs;
+  std::vector<TcTask> tt;
+  std::vector<TcTile> tiles;
+  std::vector<GemmTask> zero_k;
   double flops = 0.0;
   for (const GemmTask& t : tasks) {
     if (t.M <= 0 || t.N <= 0) continue;
     validate(t);
-    flops += 2.0 * t.M * (double)t.N * std::max(t.K, 0);
-    gemm_tc_tiles(t, (int)kept.size(), tiles);
-    kept.push_back(t);
+    if (t.K <= 0) { zero_k.push_back(t); continue; }
+    flops += 2.0 * t.M * (double)t.N * t.K;
+    const int nmb = (t.M + BM - 1) / BM, nnb = (t.N + BN - 1) / BN, nks = (t.K + kslice - 1) / kslice;
+    char* pa = ar.alloc<char>((size_t)nmb * nks * planes * BLOCK_BYTES);
+    char* pb = ar.alloc<char>((size_t)nnb * nks * planes * BLOCK_BYTES);
+    for (int rb = 0; rb < nmb; rb++)
+      for (int ks = 0; ks < nks; ks++) {
+        char* h = pa + ((size_t)rb * nks + ks) * planes * BLOCK_BYTES;
+        packs.push_back({t.A, t.lda, t.transA, t.M, t.K, rb, ks, h,
+                         planes == 2 ? h + BLOCK_BYTES : nullptr});
+      }
+    for (int nb = 0; nb < nnb; nb++)
+      for (int ks = 0; ks < nks; ks++) {
+        char* h = pb + ((size_t)nb * nks + ks) * planes * BLOCK_BYTES;
+        packs.push_back({t.B, t.ldb, !t.transB, t.N, t.K, nb, ks, h,
+                         planes == 2 ? h + BLOCK_BYTES : nullptr});
+      }
+    const int ti = (int)tt.size();
+    tt.push_back({pa, pb, t.C, t.ldc, t.M, t.N, nks, t.alpha, t.beta});
+    for (int nb = 0; nb < nnb; nb++)
+      for (int rb = 0; rb < nmb; rb++) tiles.push_back({ti, rb, nb});
   }
+  if (!zero_k.empty()) run_gemms(ar, zero_k, s);  // C = beta C
   if (tiles.empty()) return;
-  launch_gemm_tc(upload(ar, kept, s), upload(ar, tiles, s), (int)tiles.size(), split, d_err, s,
-                 flops);
+  {
+    Prof p("k_tc_pack", 0.0, (double)packs.size() * (2.0 * BLOCK_BYTES * planes), s);
+    k_tc_pack<<<(int)packs.size(), 128, 0, s>>>(upload(ar, packs, s), mode);
+    CK_LAUNCH("k_tc_pack");
+  }
+  int dev = 0, nsm = 1;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  set_max_dynamic_smem((const void*)k_gemm_tc, (int)gemm_tc_smem());
+  // test hook: a lower reporting limit for the pipeline waits (see above)
+  long long soft = SPIN_LIMIT;
+  if (const char* e = std::getenv("IFMM_TC_SOFT_WAIT_POLLS")) {
+    const long long v = std::atoll(e);
+    if (v >= 1) soft = std::min(v, SPIN_LIMIT);
+  }
+  const int grid = std::min((int)tiles.size(), nsm);
+  const char* name = mode == MODE_SPLIT ? "k_gemm_tc_3xtf32" : (mode == MODE_BF16 ? "k_gemm_tc_bf16"
+                                                                                 : "k_gemm_tc_tf32");
+  Prof p(name, flops, 0.0, s);
+  k_gemm_tc<<<grid, NTHREADS, gemm_tc_smem(), s>>>(upload(ar, tt, s), upload(ar, tiles, s),
+                                                   (int)tiles.size(), mode, d_err, soft);
+  CK_LAUNCH("k_gemm_tc");
 }
 
 }  // namespace ifmm

@@ -162,7 +162,9 @@ GraphCache::~GraphCache() {
 
 void run_graph(GraphCache& g, long long key, const char* name, cudaStream_t s,
                const std::function<void(cudaStream_t)>& body) {
-  if (!graphs_enabled()) {
+  // while the launch profile records, run the body eagerly so that every
+  // kernel gets its own event pair (a graph replay would be one interval)
+  if (!graphs_enabled() || prof::enabled()) {
     body(s);
     return;
   }

@@ -160,8 +160,10 @@ ifmm_system* system_create(ifmm_ctx* ctx, const double* pts, bool host, long lon
   require(opt->leaf_max >= 1, "leaf_max must be >= 1");
   require(opt->eps >= 0.0 && std::isfinite(opt->eps), "eps must be >= 0");
   require(opt->schur >= IFMM_P_FP64 && opt->schur <= IFMM_P_FP32, "unknown Schur precision");
-  if (opt->schur == IFMM_P_BF16)
-    throw Error(IFMM_ERR_UNSUPPORTED, "BF16 Schur products are not implemented");
+  // BF16 keeps 8 significant bits: the products are accurate to ~4e-3, so the
+  // option is offered only for loose tolerances
+  require(opt->schur != IFMM_P_BF16 || opt->eps >= 1e-4,
+          "BF16 Schur products need eps >= 1e-4");
   require(opt->rank_cap >= 0, "rank_cap must be >= 0");
   require(opt->symmetric == 0 || opt->symmetric == 1, "symmetric must be 0 or 1");
   require(opt->rsvd_rows >= 0 && opt->rsvd_rows <= 65536, "rsvd_rows must be in 0..65536");

@@ -130,7 +130,7 @@ def paper(a):
     for k, n in enumerate(orders):
         w = workloads.paper_cube(N, a.d, max(n, 1), leaf_max=a.leaf)
         opt = ifmm.make_options(dim=3, cheb_n=max(n, 1), leaf_max=w.leaf_max, eps=w.eps,
-                                fmm_n=a.fmm_n)
+                                fmm_n=a.fmm_n, rank_cap=a.rank_cap)
         s = ifmm.ifmm_system_create(ctx, torch.tensor(w.points, device="cuda"),
                                     ifmm.Kernel(w.kernel.kind, w.kernel.param, w.kernel.diag), opt)
         b = torch.tensor(w.rhs(1)[:, 0], device="cuda")

@@ -5,9 +5,9 @@
    every transpose combination, and beta != 0.  The bound is the rounding of
    the inputs plus FP32 accumulation: per element
        |C - C_ref| <= (u_in + K 2^-24) * (|alpha| |op(A)| |op(B)|)_ij + |beta| 2^-52 |C|
-   with u_in = 2 * 2^-11 for TF32 (both operands rounded to 10 mantissa bits)
-   and u_in = 4 * 2^-22 for the split product (the dropped lo*lo term and the
-   rounding of the tails).
+   with u_in = 2 * 2^-11 for TF32 (both operands rounded to 10 mantissa bits),
+   u_in = 4 * 2^-22 for the split product (the dropped lo*lo term and the
+   rounding of the tails) and u_in = 2 * 2^-8 for BF16 (7 mantissa bits).
 2. The factorisation with TF32 / split-TF32 Schur products used as the GMRES
    preconditioner: FP64 GMRES must still reach the 1e-10 residual, and its
    solution must agree with the FP64 path's to the accuracy the residual
@@ -34,10 +34,10 @@ def ctx():
 
 
 SHAPES = [(1, 1, 1), (128, 128, 32), (200, 130, 45), (257, 300, 97), (64, 700, 33),
-          (430, 430, 32), (100, 90, 0)]
+          (430, 430, 32), (100, 90, 0), (1500, 1300, 150)]   # the last: more tiles than SMs
 
 
-@pytest.mark.parametrize("prec", [ifmm.P_TF32, ifmm.P_FP32])
+@pytest.mark.parametrize("prec", [ifmm.P_TF32, ifmm.P_FP32, ifmm.P_BF16])
 @pytest.mark.parametrize("M,N,K", SHAPES)
 @pytest.mark.parametrize("tA,tB", [(0, 0), (1, 0), (0, 1), (1, 1)])
 def test_schur_product_kernel(ctx, prec, M, N, K, tA, tB):
@@ -59,7 +59,8 @@ def test_schur_product_kernel(ctx, prec, M, N, K, tA, tB):
     torch.cuda.synchronize()
     out_mem = dC.cpu().numpy()
     got = out_mem[:N, :M].T
-    u_in = 2 * 2.0 ** -11 if prec == ifmm.P_TF32 else 4 * 2.0 ** -22
+    u_in = {ifmm.P_TF32: 2 * 2.0 ** -11, ifmm.P_FP32: 4 * 2.0 ** -22,
+            ifmm.P_BF16: 2 * 2.0 ** -8}[prec]
     tol = (u_in + K * 2.0 ** -24) * bound_mat + abs(beta) * 2.0 ** -52 * np.abs(C0) + 1e-300
     err = np.abs(got - ref)
     assert np.all(err <= tol), f"max err/tol {np.max(err / tol):.3g}"
@@ -207,3 +208,30 @@ def test_fp32_substitution_sweeps(ctx, name):
             ifmm.ifmm_factor_destroy(fac)
     finally:
         ifmm.ifmm_system_destroy(sys)
+
+
+def test_bf16_schur_products_at_loose_eps(ctx):
+    """BF16 Schur products (allowed from eps = 1e-4 up): the factorisation at
+    eps = 1e-3 still preconditions FP64 GMRES to a true residual of 1e-10, and
+    a tighter eps is refused."""
+    w = small_cube(3000, 7, cheb_n=3, leaf_max=32, eps=1e-3)
+    with pytest.raises(ifmm.IFMMError) as e:
+        ifmm.ifmm_system_create(ctx, cuda(w.points), kernel(w), opts(w, eps=1e-6,
+                                                                     schur=ifmm.P_BF16))
+    assert e.value.status == 1
+    b = cuda(w.rhs(1)[:, 0])
+    its = {}
+    for prec in (ifmm.P_FP64, ifmm.P_BF16):
+        sys = ifmm.ifmm_system_create(ctx, cuda(w.points), kernel(w), opts(w, schur=prec))
+        try:
+            fac = ifmm.ifmm_factor(ctx, sys)
+            try:
+                x = torch.empty_like(b)
+                rep = ifmm.gmres_solve(ctx, sys, fac, ifmm.MV_FMM, b, x, w.N, 1e-10, 300)[0]
+                assert rep.status == 0 and rep.true_rel_residual <= 1e-10
+                its[prec] = rep.iters
+            finally:
+                ifmm.ifmm_factor_destroy(fac)
+        finally:
+            ifmm.ifmm_system_destroy(sys)
+    print(f"eps 1e-3: GMRES iterations FP64 Schur {its[ifmm.P_FP64]}, BF16 {its[ifmm.P_BF16]}")
