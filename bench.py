@@ -50,6 +50,7 @@ UNIT = "solves/s"
 N_SYSTEMS = 64
 RATE = 2000.0              # requests per second
 BUDGET = 160 * 10 ** 9     # device bytes admitted by the server
+RESIDENT_SHARE = 0.7       # of the budget for resident systems; the rest for GMRES blocks
 SERVE_CAP = 54             # rank cap 2 n^D of the serving systems (n = 3, D = 3)
 SERVE_MAXIT = 200
 
@@ -301,7 +302,8 @@ def serving_description():
             "unit cube, A_ij=1/r, A_ii=2N^(1/3), leaves<=64, Chebyshev 3^3, eps=1e-6, rank cap "
             f"{SERVE_CAP}, split-TF32 Schur, symmetric; Poisson arrivals {RATE:g}/s, 1-32 "
             "standard-normal RHS per request, GMRES to true residual 1e-10, "
-            f"{BUDGET / 1e9:g} GB device budget")
+            f"{BUDGET / 1e9:g} GB device budget ({RESIDENT_SHARE:.0%} for resident systems, the rest "
+            "for GMRES blocks)")
 
 
 class Load:
@@ -381,6 +383,7 @@ def run_serving(args, ifmm, torch, ctx, dev, world, rank, dist):
     opt = ifmm.make_options(dim=3, cheb_n=3, leaf_max=64, eps=1e-6, schur=schur, symmetric=1,
                             rank_cap=SERVE_CAP)
     srv = ifmm.ifmm_server_create(ctx, BUDGET, workers=args.workers)
+    ifmm.ifmm_server_set_reserve(srv, int((1.0 - RESIDENT_SHARE) * BUDGET))
     try:
         return _serve(args, ifmm, torch, ctx, dev, world, rank, dist, ws, N, n_serve, opt, srv)
     finally:
@@ -400,7 +403,8 @@ def _serve(args, ifmm, torch, ctx, dev, world, rank, dist, ws, N, n_serve, opt, 
         while k < len(order) and len(group) < 8:
             s = order[k]
             k += 1
-            if bytes_per_point is not None and admitted_bytes + 1.05 * bytes_per_point * N[s] > BUDGET:
+            if (bytes_per_point is not None and
+                    admitted_bytes + 1.05 * bytes_per_point * N[s] > RESIDENT_SHARE * BUDGET):
                 continue
             group.append(s)
         if not group:

@@ -112,6 +112,10 @@ typedef struct {
                  IFMM_P_FP32: FP32 sweeps (FP32 copies of the factors, made on
                  first use), valid only with IFMM_GMRES_FLEXIBLE; products,
                  orthogonalisation and residuals stay FP64                      */
+  int block;  /* 1: block GMRES -- one Krylov space shared by the nrhs columns
+                 (block Arnoldi, block CGS2, Cholesky QR twice); right or
+                 flexible side; maxit counts block steps; columns still above
+                 tol when a block loses rank finish with per-column GMRES     */
 } ifmm_gmres_options;
 
 typedef struct {
@@ -307,10 +311,13 @@ ifmm_status ifmm_server_create(ifmm_ctx* ctx, unsigned long long hbm_budget, int
 ifmm_status ifmm_server_create_ex(ifmm_ctx* ctx, unsigned long long hbm_budget, int workers,
                                   int precond_precision, ifmm_server** out);
 void ifmm_server_destroy(ifmm_server* srv);
+/* Keeps `bytes` of the budget out of later registrations, for the GMRES
+ * memory of blocks (default 0; at most the budget). */
+ifmm_status ifmm_server_set_reserve(ifmm_server* srv, unsigned long long bytes);
 /* Admits (sys, fac) if its resident device memory -- operators,
  * factorisation, solve plans and (FP32 server) the FP32 copies of the
- * factors, which this call builds -- fits what is left of hbm_budget;
- * IFMM_ERR_BUDGET otherwise (nothing is registered).  maxit: the largest
+ * factors, which this call builds -- fits what is left of hbm_budget less
+ * the reserve; IFMM_ERR_BUDGET otherwise (nothing is registered).  maxit: the largest
  * maxit its requests will use.  A system or factorisation registered twice is
  * IFMM_ERR_INVALID_ARG.  The server does not own sys or fac; they must outlive it.
  * *id: the handle for ifmm_server_submit. */

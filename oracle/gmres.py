@@ -81,3 +81,48 @@ def gmres(matvec, b: np.ndarray, precond=None, tol: float = 1e-10, maxit: int = 
     y = np.linalg.solve(np.triu(H[:k, :k]), g[:k]) if k else np.zeros(0)
     x = V[:k].T @ y if left else M(V[:k].T @ y)
     return x, k, res / beta
+
+
+def block_gmres(matvec, B: np.ndarray, precond=None, tol: float = 1e-10, maxit: int = 500):
+    """Block GMRES with a right preconditioner: one Krylov space
+    span{R0, A P^-1 R0, ...} shared by the k columns of B (x_0 = 0).  Block
+    Arnoldi with classical Gram-Schmidt applied twice and a QR of every new
+    block; the least-squares problem min |E_1 S_0 - H Y| is solved afresh at
+    each step (numpy lstsq), a column converging when its residual there is at
+    most tol ||b_c||.  Returns (X, block steps, relative residual estimates)."""
+    B = np.asarray(B, dtype=np.float64)
+    if B.ndim == 1:
+        B = B[:, None]
+    n, k = B.shape
+    M = precond if precond is not None else (lambda v: v)
+    Mb = lambda V: np.column_stack([M(V[:, c]) for c in range(V.shape[1])])
+    Ab = lambda V: np.column_stack([matvec(V[:, c]) for c in range(V.shape[1])])
+    bn = np.linalg.norm(B, axis=0)
+    V0, S0 = np.linalg.qr(B)
+    Vs = [V0]
+    H = np.zeros(((maxit + 1) * k, maxit * k))
+    res = bn.copy()
+    Y = np.zeros((0, k))
+    j = 0
+    for j in range(maxit):
+        W = Ab(Mb(Vs[j]))
+        Vall = np.hstack(Vs)
+        h = Vall.T @ W
+        W = W - Vall @ h
+        h2 = Vall.T @ W
+        W = W - Vall @ h2
+        Vn, Rn = np.linalg.qr(W)
+        Vs.append(Vn)
+        H[:(j + 1) * k, j * k:(j + 1) * k] = h + h2
+        H[(j + 1) * k:(j + 2) * k, j * k:(j + 1) * k] = Rn
+        E = np.zeros(((j + 2) * k, k))
+        E[:k] = S0
+        Hj = H[:(j + 2) * k, :(j + 1) * k]
+        Y = np.linalg.lstsq(Hj, E, rcond=None)[0]
+        res = np.linalg.norm(E - Hj @ Y, axis=0)
+        if np.all(res <= tol * bn):
+            break
+    steps = j + 1
+    X = Mb(np.hstack(Vs[:steps]) @ Y)
+    return X, steps, res / np.where(bn > 0, bn, 1.0)
+

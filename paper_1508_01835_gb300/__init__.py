@@ -44,7 +44,8 @@ class GmresReport(C.Structure):
 
 
 class GmresOptions(C.Structure):
-    _fields_ = [("side", C.c_int), ("refine", C.c_int), ("precond_precision", C.c_int)]
+    _fields_ = [("side", C.c_int), ("refine", C.c_int), ("precond_precision", C.c_int),
+                ("block", C.c_int)]
 
 
 class SystemInfo(C.Structure):
@@ -124,6 +125,7 @@ def lib() -> C.CDLL:
         "ifmm_server_submit_device": (C.c_int, [P, C.c_int, P, P, C.c_int, C.c_double, C.c_int,
                                                 C.POINTER(C.c_longlong)]),
         "ifmm_server_destroy": (None, [P]),
+        "ifmm_server_set_reserve": (C.c_int, [P, C.c_ulonglong]),
         "ifmm_server_register": (C.c_int, [P, P, P, C.c_int, C.POINTER(C.c_int)]),
         "ifmm_server_submit": (C.c_int, [P, C.c_int, P, P, C.c_int, C.c_double, C.c_int,
                                          C.POINTER(C.c_longlong)]),
@@ -308,12 +310,12 @@ def gmres_solve(ctx, sys, fac, mode: int, b, x, N: int, tol=1e-10, maxit=500, st
 
 
 def gmres_solve_ex(ctx, sys, fac, mode: int, b, x, N: int, tol=1e-10, maxit=500,
-                   side=GMRES_RIGHT, refine=2, precond_precision=P_FP64, stream=None):
+                   side=GMRES_RIGHT, refine=2, precond_precision=P_FP64, block=0, stream=None):
     pb, k, ld = _vec(b, N)
     px, k2, _ = _vec(x, N)
     assert k == k2
     reps = (GmresReport * k)()
-    o = GmresOptions(side, refine, precond_precision)
+    o = GmresOptions(side, refine, precond_precision, block)
     _check(lib().gmres_solve_ex(ctx, sys, fac, mode, pb, px, k, ld, tol, maxit, C.byref(o), reps,
                                 _stream(stream)), ctx, allow=(5,))
     return list(reps)
@@ -365,6 +367,10 @@ def ifmm_server_create(ctx, hbm_budget: int, workers: int = 0, precond_precision
 
 def ifmm_server_destroy(srv):
     lib().ifmm_server_destroy(srv)
+
+
+def ifmm_server_set_reserve(srv, nbytes: int):
+    _scheck(lib().ifmm_server_set_reserve(srv, nbytes), srv)
 
 
 def ifmm_server_register(srv, sys, fac, maxit: int = 100) -> int:

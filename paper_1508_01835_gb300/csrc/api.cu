@@ -217,6 +217,8 @@ ifmm_status gmres_solve(ifmm_ctx* ctx, const ifmm_system* sys, const ifmm_factor
   ifmm_status res = IFMM_OK;
   ifmm_status g = guard(ctx, [&] {
     CK(cudaSetDevice(ctx->device));
+    // the caller's vectors join the bounds validation (IFMM_VALIDATE=1)
+    ScopedRange rb(b, mat_bytes(sys->N, nrhs, ld)), rx(x, mat_bytes(sys->N, nrhs, ld));
     res = gmres_run(const_cast<ifmm_system*>(sys), const_cast<ifmm_factorization*>(fac), mode, b,
                     x, nrhs, ld, tol, maxit, rep, st(stream));
   });
@@ -242,10 +244,14 @@ ifmm_status gmres_solve_ex(ifmm_ctx* ctx, const ifmm_system* sys, const ifmm_fac
     go.side = opt->side;
     go.refine = opt->refine;
     go.precond_fp32 = opt->precond_precision == IFMM_P_FP32;
+    if (opt->block != 0 && opt->block != 1) return IFMM_ERR_INVALID_ARG;
+    if (opt->block && fac && opt->side == IFMM_GMRES_LEFT) return IFMM_ERR_INVALID_ARG;
+    go.block = opt->block;
   }
   ifmm_status res = IFMM_OK;
   ifmm_status g = guard(ctx, [&] {
     CK(cudaSetDevice(ctx->device));
+    ScopedRange rb(b, mat_bytes(sys->N, nrhs, ld)), rx(x, mat_bytes(sys->N, nrhs, ld));
     res = gmres_run(const_cast<ifmm_system*>(sys), const_cast<ifmm_factorization*>(fac), mode, b,
                     x, nrhs, ld, tol, maxit, rep, st(stream), nullptr, go);
   });

@@ -121,6 +121,7 @@ struct ifmm_server {
   int device = 0;
   int precond_fp32 = 1;  // flexible GMRES with FP32 substitution sweeps
   size_t budget = 0, used = 0;  // used: resident systems (operators, factors, plans)
+  size_t reserve = 0;           // kept from registrations for the GMRES blocks
   int col_cap = 32;
   int queue_cap = 32;  // queued columns per system (one block) beyond which requests are shed
   long long shed = 0, refused = 0;
@@ -140,11 +141,12 @@ struct ifmm_server {
   std::vector<std::thread> workers;
   std::string last_error;
 
-  // device bytes a block of `width` columns may use: Krylov basis (and the
-  // preconditioned basis of flexible GMRES) of maxit + 1 vectors in chunks of
-  // 16, four work vectors, the block's b and x
+  // device bytes a block of `width` columns is admitted with: the Krylov basis
+  // (and the preconditioned basis of flexible GMRES) in chunks of 16 vectors
+  // up to the first 64 vectors, four work vectors, the block's b and x.  A
+  // block that iterates further grows its workspace by a chunk at a time.
   size_t block_bytes(long long N, int width, int maxit) const {
-    const long long vecs = ((maxit + 16) / 16) * 16;
+    const long long vecs = std::min<long long>(((maxit + 16) / 16) * 16, 64);
     const long long nb = precond_fp32 ? 2 : 1;
     return sizeof(double) * (size_t)N * width * (size_t)(nb * vecs + 6);
   }
@@ -411,10 +413,12 @@ ifmm_status ifmm_server_register(ifmm_server* s, ifmm_system* sys, ifmm_factoriz
     bytes += est;
   }
   std::lock_guard<std::mutex> g(s->mu);
-  if (s->used + bytes > s->budget) {
+  const size_t avail = s->budget > s->reserve ? s->budget - s->reserve : 0;
+  if (s->used + bytes > avail) {
     s->last_error = "admission refused: the system needs " + std::to_string(bytes) +
-                    " bytes of device memory, " + std::to_string(s->budget - s->used) +
-                    " remain in the budget";
+                    " bytes of device memory, " +
+                    std::to_string(avail > s->used ? avail - s->used : 0) +
+                    " remain for resident systems";
     return IFMM_ERR_BUDGET;
   }
   if (s->precond_fp32 && !fac->f32.ready) {
@@ -501,6 +505,14 @@ ifmm_status ifmm_server_wait(ifmm_server* s, long long ticket, int timeout_ms,
   const ifmm_status st = r->status;
   s->reqs.erase(it);
   return st;
+}
+
+ifmm_status ifmm_server_set_reserve(ifmm_server* s, unsigned long long bytes) {
+  if (!s) return IFMM_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> g(s->mu);
+  if (bytes > s->budget) return IFMM_ERR_INVALID_ARG;
+  s->reserve = bytes;
+  return IFMM_OK;
 }
 
 ifmm_status ifmm_server_stats(ifmm_server* s, unsigned long long* used_bytes, long long* batches,

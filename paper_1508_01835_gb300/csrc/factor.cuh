@@ -115,9 +115,13 @@ struct GmresOpts {
   int side = IFMM_GMRES_RIGHT;  // ifmm_gmres_side
   int refine = 2;               // restarts from x when the true residual misses tol
   int precond_fp32 = 0;         // substitution sweeps in FP32 (flexible GMRES only)
+  int block = 0;                // block GMRES over the columns
 };
 ifmm_status gmres_run(ifmm_system* sys, ifmm_factorization* fac, int mode, const double* b,
                       double* x, int nrhs, long long ld, double tol, int maxit,
                       ifmm_gmres_report* rep, cudaStream_t s, Arena* workspace = nullptr,
                       const GmresOpts& opt = GmresOpts());
+ifmm_status block_gmres_run(ifmm_system* sys, ifmm_factorization* fac, int mode, const double* b,
+                            double* x, int k, long long ld, double tol, int maxit,
+                            ifmm_gmres_report* rep, cudaStream_t s, const GmresOpts& opt);
 }  // namespace ifmm

@@ -165,6 +165,11 @@ ifmm_status gmres_run(ifmm_system* sys, ifmm_factorization* fac, int mode, const
                       double* x, int nrhs, long long ld, double tol, int maxit,
                       ifmm_gmres_report* rep, cudaStream_t s, Arena* workspace,
                       const GmresOpts& opt) {
+  if (opt.block && nrhs > 1) {
+    GmresOpts bo = opt;
+    bo.block = 0;  // the per-column finish of block GMRES
+    return block_gmres_run(sys, fac, mode, b, x, nrhs, ld, tol, maxit, rep, s, bo);
+  }
   const long long N = sys->N;
   const int m = maxit;
   const int side = fac ? opt.side : IFMM_GMRES_RIGHT;  // no preconditioner: plain GMRES
@@ -324,6 +329,296 @@ ifmm_status gmres_run(ifmm_system* sys, ifmm_factorization* fac, int mode, const
     const bool conv = side == IFMM_GMRES_LEFT ? est_ok
                                               : (est_ok && rep[c].true_rel_residual <= tol);
     rep[c].status = conv ? IFMM_OK : IFMM_ERR_NOT_CONVERGED;
+    if (!conv) out = IFMM_ERR_NOT_CONVERGED;
+  }
+  return out;
+}
+
+
+// ---------------------------------------------------------------------------
+// Block GMRES over the nrhs columns (one Krylov space shared by all right-hand
+// sides; right or flexible preconditioning): block Arnoldi with block CGS2 and
+// Cholesky QR (applied twice) of each new block, the block Hessenberg reduced
+// by Givens rotations on the host (it is at most a few thousand entries
+// wide), x = M^-1 V Y (right) or Z Y (flexible).  A column's residual is the
+// norm of its part of the rotated right-hand side below the triangle.  If a
+// new block loses rank (Cholesky breaks down, e.g. after some columns have
+// converged) the block iteration stops and the columns still above tol finish
+// with the per-column GMRES from the current x.
+// ---------------------------------------------------------------------------
+__global__ void k_sum_parts(const double* __restrict__ part, int nparts, long long n,
+                            double* __restrict__ out) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int c = 0; c < nparts; c++) s += part[(long long)c * n + e];
+    out[e] = s;
+  }
+}
+
+// D (m x k, ld m) = X^T Y, X: N x m (ld ldx), Y: N x k (ld ldy); split over
+// row chunks of N, partial products summed in chunk order (deterministic)
+static void gram(Arena& ar, const double* X, long long ldx, int m, const double* Y, long long ldy,
+                 int k, long long N, double* D, cudaStream_t s) {
+  const long long chunk = std::max<long long>(2048, (N + 63) / 64);
+  const int nparts = (int)((N + chunk - 1) / chunk);
+  double* part = ar.alloc<double>((size_t)nparts * m * k);
+  std::vector<GemmTask> g;
+  for (int c = 0; c < nparts; c++) {
+    const long long r0 = (long long)c * chunk, r1 = std::min(N, r0 + chunk);
+    g.push_back(GemmTask{X + r0, Y + r0, part + (size_t)c * m * k, (int)ldx, (int)ldy, m, m, k,
+                         (int)(r1 - r0), 1, 0, 1.0, 0.0});
+  }
+  run_gemms(ar, g, s);
+  const long long n = (long long)m * k;
+  k_sum_parts<<<(int)std::min<long long>(1024, (n + 255) / 256), 256, 0, s>>>(part, nparts, n, D);
+  CK_LAUNCH("k_sum_parts");
+}
+
+// Cholesky G = R^T R (k x k, column-major); false if not positive definite
+static bool chol_upper(const std::vector<double>& G, int k, std::vector<double>& R) {
+  R.assign((size_t)k * k, 0.0);
+  for (int j = 0; j < k; j++) {
+    double d = G[j + (size_t)j * k];
+    for (int i = 0; i < j; i++) d -= R[i + (size_t)j * k] * R[i + (size_t)j * k];
+    if (!(d > 1e-300)) return false;
+    const double rjj = std::sqrt(d);
+    R[j + (size_t)j * k] = rjj;
+    for (int c = j + 1; c < k; c++) {
+      double v = G[j + (size_t)c * k];
+      for (int i = 0; i < j; i++) v -= R[i + (size_t)j * k] * R[i + (size_t)c * k];
+      R[j + (size_t)c * k] = v / rjj;
+    }
+  }
+  return true;
+}
+
+static std::vector<double> inv_upper(const std::vector<double>& R, int k) {
+  std::vector<double> X((size_t)k * k, 0.0);
+  for (int c = 0; c < k; c++) {  // solve R x = e_c
+    for (int i = c; i >= 0; i--) {
+      double v = (i == c) ? 1.0 : 0.0;
+      for (int j = i + 1; j <= c; j++) v -= R[i + (size_t)j * k] * X[j + (size_t)c * k];
+      X[i + (size_t)c * k] = v / R[i + (size_t)i * k];
+    }
+  }
+  return X;
+}
+
+ifmm_status block_gmres_run(ifmm_system* sys, ifmm_factorization* fac, int mode, const double* b,
+                            double* x, int k, long long ld, double tol, int maxit,
+                            ifmm_gmres_report* rep, cudaStream_t s, const GmresOpts& opt) {
+  const long long N = sys->N;
+  const bool flex = fac && opt.side == IFMM_GMRES_FLEXIBLE;
+  if (fac && opt.side == IFMM_GMRES_LEFT)
+    throw Error(IFMM_ERR_INVALID_ARG, "block GMRES takes right or flexible preconditioning");
+  const int m = maxit;  // block steps
+  Arena ar;
+  ar.chunk_bytes = size_t(64) << 20;
+  Arena scratch;
+  double* V = ar.alloc<double>((size_t)N * (m + 1) * k);      // basis blocks, ld N
+  double* Zall = flex ? ar.alloc<double>((size_t)N * m * k) : nullptr;
+  double* Zt = ar.alloc<double>((size_t)N * k);
+  double* W = ar.alloc<double>((size_t)N * k);
+  double* D = ar.alloc<double>((size_t)(m + 1) * k * k);
+  double* D2 = ar.alloc<double>((size_t)(m + 1) * k * k);
+  double* Gk = ar.alloc<double>((size_t)k * k);
+  double* Ri = ar.alloc<double>((size_t)k * k);
+  auto precond = [&](const double* in, long long ldi, double* out, long long ldo) {
+    if (!fac) launch_axpby(N, k, nullptr, 1.0, in, ldi, 0.0, out, ldo, s);
+    else if (opt.precond_fp32) factor_solve_f32(fac, in, ldi, out, ldo, k, s);
+    else factor_solve(fac, in, ldi, out, ldo, k, s);
+  };
+  // column norms of b (stopping references)
+  std::vector<double> bn(k);
+  {
+    double* hn = scratch.alloc<double>(k);
+    double* part = scratch.alloc<double>((size_t)256 * k);
+    launch_dots(b, ld, b, ld, N, k, hn, part, s);
+    CK(cudaMemcpyAsync(bn.data(), hn, k * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (auto& v : bn) v = std::sqrt(v);
+  }
+  // Cholesky QR twice of the block at W into V_j, returning R (k x k) = R2 R1
+  auto cholqr2 = [&](double* Vj, std::vector<double>& Rtot) -> bool {
+    std::vector<double> R1, R2, Gh((size_t)k * k);
+    for (int pass = 0; pass < 2; pass++) {
+      scratch.reset();
+      gram(scratch, W, N, k, W, N, k, N, Gk, s);
+      CK(cudaMemcpyAsync(Gh.data(), Gk, sizeof(double) * k * k, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      std::vector<double>& R = pass == 0 ? R1 : R2;
+      if (!chol_upper(Gh, k, R)) return false;
+      std::vector<double> Rinv = inv_upper(R, k);
+      CK(cudaMemcpyAsync(Ri, Rinv.data(), sizeof(double) * k * k, cudaMemcpyHostToDevice, s));
+      double* dst = pass == 0 ? Zt : Vj;  // W R1^-1 -> Zt -> (copy back) ; second pass -> V_j
+      run_gemms(scratch, {GemmTask{W, Ri, dst, (int)N, k, (int)N, (int)N, k, k, 0, 0, 1.0, 0.0}}, s);
+      if (pass == 0) launch_axpby(N, k, nullptr, 1.0, Zt, N, 0.0, W, N, s);
+      CK(cudaStreamSynchronize(s));
+    }
+    Rtot.assign((size_t)k * k, 0.0);  // R2 R1
+    for (int c = 0; c < k; c++)
+      for (int r = 0; r <= c; r++) {
+        double v = 0.0;
+        for (int q = r; q <= c; q++) v += R2[r + (size_t)q * k] * R1[q + (size_t)c * k];
+        Rtot[r + (size_t)c * k] = v;
+      }
+    return true;
+  };
+  // host state of the least-squares problem: rotated block Hessenberg columns
+  const int rows = (m + 1) * k;
+  std::vector<double> Hh((size_t)rows * m * k, 0.0);  // column-major, ld rows
+  std::vector<double> G((size_t)rows * k, 0.0);       // rotated right-hand side
+  struct Rot { int r; double c, s; };
+  std::vector<Rot> rots;
+  std::vector<int> first_ok(k, -1);
+  // V_0 S_0 = b
+  launch_axpby(N, k, nullptr, 1.0, b, ld, 0.0, W, N, s);
+  std::vector<double> S0;
+  if (!cholqr2(V, S0)) throw Error(IFMM_ERR_INVALID_ARG, "block GMRES: the right-hand sides are linearly dependent");
+  for (int c = 0; c < k; c++)
+    for (int r = 0; r <= c; r++) G[r + (size_t)c * rows] = S0[r + (size_t)c * k];
+  int steps = 0;
+  bool broke = false;
+  for (int j = 0; j < m; j++) {
+    double* Vj = V + (size_t)j * k * N;
+    double* Zj = flex ? Zall + (size_t)j * k * N : Zt;
+    precond(Vj, N, Zj, N);
+    system_matvec(sys, mode, Zj, N, W, N, k, s);
+    // block CGS2 against V_0 .. V_j
+    const int mj = (j + 1) * k;
+    scratch.reset();
+    gram(scratch, V, N, mj, W, N, k, N, D, s);
+    run_gemms(scratch, {GemmTask{V, D, W, (int)N, mj, (int)N, (int)N, k, mj, 0, 0, -1.0, 1.0}}, s);
+    gram(scratch, V, N, mj, W, N, k, N, D2, s);
+    run_gemms(scratch, {GemmTask{V, D2, W, (int)N, mj, (int)N, (int)N, k, mj, 0, 0, -1.0, 1.0}}, s);
+    std::vector<double> h1((size_t)mj * k), h2((size_t)mj * k);
+    CK(cudaMemcpyAsync(h1.data(), D, sizeof(double) * mj * k, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(h2.data(), D2, sizeof(double) * mj * k, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    std::vector<double> Rn;
+    const bool ok = cholqr2(V + (size_t)(j + 1) * k * N, Rn);
+    // new block column of H: [h1 + h2 ; R_{j+1,j}]
+    for (int c = 0; c < k; c++) {
+      double* col = Hh.data() + (size_t)(j * k + c) * rows;
+      for (int r = 0; r < mj; r++) col[r] = h1[r + (size_t)c * mj] + h2[r + (size_t)c * mj];
+      for (int r = 0; r < k; r++) col[mj + r] = ok ? Rn[r + (size_t)c * k] : 0.0;
+    }
+    // apply the earlier blocks' rotations (in creation order) to the whole new
+    // block column, then zero its subdiagonal entries column by column
+    for (int c = 0; c < k; c++) {
+      double* col = Hh.data() + (size_t)(j * k + c) * rows;
+      for (const Rot& q : rots) {
+        const double a = col[q.r], bb = col[q.r + 1];
+        col[q.r] = q.c * a + q.s * bb;
+        col[q.r + 1] = -q.s * a + q.c * bb;
+      }
+    }
+    for (int c = 0; c < k; c++) {
+      double* col = Hh.data() + (size_t)(j * k + c) * rows;
+      const int dg = j * k + c;  // diagonal row of this column
+      for (int r = mj + c; r > dg; r--) {
+        const double a = col[r - 1], bb = col[r];
+        const double den = std::hypot(a, bb);
+        const double cc = den != 0.0 ? a / den : 1.0, ss = den != 0.0 ? bb / den : 0.0;
+        col[r - 1] = den;
+        col[r] = 0.0;
+        rots.push_back({r - 1, cc, ss});
+        for (int q = 0; q < k; q++) {
+          double* g = G.data() + (size_t)q * rows;
+          const double ga = g[r - 1], gb = g[r];
+          g[r - 1] = cc * ga + ss * gb;
+          g[r] = -ss * ga + cc * gb;
+        }
+        // the rotation also acts on the later columns of this block
+        for (int c2 = c + 1; c2 < k; c2++) {
+          double* o = Hh.data() + (size_t)(j * k + c2) * rows;
+          const double oa = o[r - 1], ob = o[r];
+          o[r - 1] = cc * oa + ss * ob;
+          o[r] = -ss * oa + cc * ob;
+        }
+      }
+    }
+    steps = j + 1;
+    // residuals of the columns: their parts of G below row (j + 1) k
+    bool all = true;
+    for (int q = 0; q < k; q++) {
+      double rr = 0.0;
+      for (int r = (j + 1) * k; r < (j + 2) * k; r++) rr += G[r + (size_t)q * rows] * G[r + (size_t)q * rows];
+      const double res = std::sqrt(rr);
+      rep[q].rel_residual = bn[q] > 0 ? res / bn[q] : 0.0;
+      if (bn[q] == 0.0 || res <= tol * bn[q]) {
+        if (first_ok[q] < 0) first_ok[q] = steps;
+      } else {
+        all = false;
+      }
+    }
+    if (all) break;
+    if (!ok) { broke = true; break; }
+  }
+  // rotations above were applied within each block column as the zeros were
+  // made, so Hh[0:n, 0:n] is upper triangular; Y = H^-1 G[0:n, :]
+  const int n = steps * k;
+  std::vector<double> Y((size_t)n * k, 0.0);
+  for (int q = 0; q < k; q++)
+    for (int i = n - 1; i >= 0; i--) {
+      double v = G[i + (size_t)q * rows];
+      for (int c = i + 1; c < n; c++) v -= Hh[i + (size_t)c * rows] * Y[c + (size_t)q * n];
+      const double d = Hh[i + (size_t)i * rows];
+      Y[i + (size_t)q * n] = d != 0.0 ? v / d : 0.0;
+    }
+  double* Yd = scratch.alloc<double>((size_t)n * k);
+  CK(cudaMemcpyAsync(Yd, Y.data(), sizeof(double) * n * k, cudaMemcpyHostToDevice, s));
+  if (flex) {
+    run_gemms(scratch, {GemmTask{Zall, Yd, x, (int)N, n, (int)ld, (int)N, k, n, 0, 0, 1.0, 0.0}}, s);
+  } else {
+    run_gemms(scratch, {GemmTask{V, Yd, W, (int)N, n, (int)N, (int)N, k, n, 0, 0, 1.0, 0.0}}, s);
+    precond(W, N, x, ld);
+  }
+  CK(cudaStreamSynchronize(s));
+  // true residuals; columns still above tol finish with per-column GMRES from x
+  double* R = W;
+  system_matvec(sys, mode, x, ld, R, N, k, s);
+  launch_axpby(N, k, nullptr, 1.0, b, ld, -1.0, R, N, s);
+  std::vector<double> rn(k);
+  {
+    double* hn = scratch.alloc<double>(k);
+    double* part = scratch.alloc<double>((size_t)256 * k);
+    launch_dots(R, N, R, N, N, k, hn, part, s);
+    CK(cudaMemcpyAsync(rn.data(), hn, k * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  ifmm_status out = IFMM_OK;
+  bool finish = false;
+  for (int q = 0; q < k; q++) {
+    rep[q].iters = first_ok[q] > 0 ? first_ok[q] : steps;
+    rep[q].true_rel_residual = bn[q] > 0 ? std::sqrt(rn[q]) / bn[q] : 0.0;
+    if (rep[q].true_rel_residual > tol) finish = true;
+  }
+  if (finish && steps < m && opt.refine > 0) {
+    // dx from the residual R (= b - A x), one column group, per-column GMRES
+    std::vector<ifmm_gmres_report> r2(k);
+    GmresOpts o2 = opt;
+    o2.side = flex ? IFMM_GMRES_FLEXIBLE : IFMM_GMRES_RIGHT;
+    double* dx = Zt;
+    gmres_run(sys, fac, mode, R, dx, k, N, tol * 0.999, m - steps, r2.data(), s, nullptr, o2);
+    (void)broke;
+    launch_axpby(N, k, nullptr, 1.0, dx, N, 1.0, x, ld, s);
+    system_matvec(sys, mode, x, ld, R, N, k, s);
+    launch_axpby(N, k, nullptr, 1.0, b, ld, -1.0, R, N, s);
+    double* hn = scratch.alloc<double>(k);
+    double* part = scratch.alloc<double>((size_t)256 * k);
+    launch_dots(R, N, R, N, N, k, hn, part, s);
+    CK(cudaMemcpyAsync(rn.data(), hn, k * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int q = 0; q < k; q++) {
+      rep[q].iters += r2[q].iters;
+      rep[q].true_rel_residual = bn[q] > 0 ? std::sqrt(rn[q]) / bn[q] : 0.0;
+    }
+  }
+  for (int q = 0; q < k; q++) {
+    const bool conv = rep[q].true_rel_residual <= tol;
+    rep[q].status = conv ? IFMM_OK : IFMM_ERR_NOT_CONVERGED;
     if (!conv) out = IFMM_ERR_NOT_CONVERGED;
   }
   return out;

@@ -75,6 +75,20 @@ struct Ranges {
     std::lock_guard<std::mutex> g(mu());
     map().erase((uintptr_t)p);
   }
+  // registers [p, p + n) unless an existing range already holds it; true if added
+  static bool add_if_uncovered(const void* p, size_t n) {
+    if (!on() || !p || n == 0) return false;
+    std::lock_guard<std::mutex> g(mu());
+    auto& m = map();
+    auto it = m.upper_bound((uintptr_t)p);
+    if (it != m.begin()) {
+      --it;
+      if ((uintptr_t)p >= it->first && (uintptr_t)p + n <= it->first + it->second) return false;
+    }
+    if (m.count((uintptr_t)p)) return false;
+    m[(uintptr_t)p] = n;
+    return true;
+  }
   static void check(const void* p, size_t bytes, const char* what) {
     if (!on() || bytes == 0) return;
     std::lock_guard<std::mutex> g(mu());
@@ -95,10 +109,15 @@ inline size_t mat_bytes(long long rows, long long cols, long long ld, size_t ele
     throw Error(IFMM_ERR_CUDA, "bounds check failed: leading dimension < rows");
   return (size_t)((cols - 1) * ld + rows) * elem;
 }
+// a caller's buffer registered for the duration of one call (left alone when a
+// registered allocation already holds it)
 struct ScopedRange {
   const void* p;
-  ScopedRange(const void* q, size_t n) : p(q) { Ranges::add(q, n); }
-  ~ScopedRange() { Ranges::remove(p); }
+  bool added;
+  ScopedRange(const void* q, size_t n) : p(q), added(Ranges::add_if_uncovered(q, n)) {}
+  ~ScopedRange() {
+    if (added) Ranges::remove(p);
+  }
 };
 
 // ---------------------------------------------------------------------------

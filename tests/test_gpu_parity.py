@@ -440,3 +440,43 @@ def test_invalid_arguments_are_rejected(ctx):
         ifmm.ifmm_system_create(ctx, pts, kernel(w), bad)
     with pytest.raises(ifmm.IFMMError):
         ifmm.ifmm_system_create(ctx, pts, ifmm.Kernel(K_INV_R, 0.0, math.nan), opts(w))
+
+
+@pytest.mark.parametrize("name", ["cube2k", "3lev"])
+def test_block_gmres_parity(ctx, name):
+    """Block GMRES (one Krylov space for four right-hand sides, right
+    preconditioning) on both sides at tol 1e-13: the same number of block
+    steps (+-1) as the oracle's block GMRES and the same solutions to 1e-10;
+    no more block steps than single-vector GMRES takes per column.  The flexible
+    form with FP32 sweeps reaches the true residual 1e-10 as well."""
+    from oracle.gmres import block_gmres
+    w = CASES[name]()
+    h2 = oracle_h2(w)
+    ora = IFMM(h2, w.eps)
+    B = w.rhs(4)
+    p = h2.tree.perm
+    mv = lambda v: to_user(h2, h2.matvec(v[p]))
+    X_o, steps_o, _ = block_gmres(mv, B, ora.solve, 1e-13, 200)
+    sys = make_sys(ctx, w, tau=ora.tau, rank_cap=1 << 20)
+    fac = ifmm.ifmm_factor(ctx, sys)
+    try:
+        Bt = cuda(B.T.copy())
+        X = torch.empty_like(Bt)
+        reps = ifmm.gmres_solve_ex(ctx, sys, fac, ifmm.MV_FMM, Bt, X, w.N, 1e-13, 200, block=1,
+                                   refine=0)
+        steps = max(r.iters for r in reps)
+        err = rel(X.cpu().numpy().T, X_o)
+        single = ifmm.gmres_solve_ex(ctx, sys, fac, ifmm.MV_FMM, Bt, torch.empty_like(Bt), w.N,
+                                     1e-13, 200, refine=0)
+        print(f"{name} block GMRES: {steps} block steps (oracle {steps_o}), single-vector "
+              f"{[r.iters for r in single]}, error vs oracle {err:.1e}")
+        assert abs(steps - steps_o) <= 1
+        assert err < 1e-10
+        assert steps <= max(r.iters for r in single)
+        X32 = torch.empty_like(Bt)
+        r32 = ifmm.gmres_solve_ex(ctx, sys, fac, ifmm.MV_FMM, Bt, X32, w.N, 1e-10, 200, block=1,
+                                  side=ifmm.GMRES_FLEXIBLE, precond_precision=ifmm.P_FP32)
+        assert all(r.status == 0 and r.true_rel_residual <= 1e-10 for r in r32)
+    finally:
+        ifmm.ifmm_factor_destroy(fac)
+        ifmm.ifmm_system_destroy(sys)

@@ -74,3 +74,27 @@ def test_left_residual_is_the_preconditioned_residual():
     # reach the dense solution
     xr, itr, _ = gmres(lambda v: A @ v, b, precond=Pinv, tol=1e-12, side="right")
     assert np.allclose(xr, x, rtol=1e-8)
+
+
+def test_block_gmres_matches_dense_solve_and_exact_preconditioner():
+    """Block GMRES: every column reaches the dense solution; with the exact
+    inverse as right preconditioner one block step solves all columns; with 4
+    generic right-hand sides of a 12 x 12 system the shared Krylov space gains
+    4 directions per step and spans the whole space after 12 / 4 = 3 steps,
+    where single-vector GMRES needs 12."""
+    from oracle.gmres import block_gmres
+    rng = np.random.default_rng(6)
+    A = rng.standard_normal((90, 90)) + 15 * np.eye(90)
+    B = rng.standard_normal((90, 3))
+    X, steps, res = block_gmres(lambda v: A @ v, B, tol=1e-12)
+    assert np.allclose(X, np.linalg.solve(A, B), rtol=1e-9, atol=1e-10)
+    Ai = np.linalg.inv(A)
+    X1, s1, _ = block_gmres(lambda v: A @ v, B, precond=lambda v: Ai @ v, tol=1e-10)
+    assert s1 == 1 and np.allclose(A @ X1, B, atol=1e-9)
+    Q, _ = np.linalg.qr(rng.standard_normal((12, 12)))
+    As = Q @ np.diag(np.arange(1.0, 13.0)) @ Q.T
+    B4 = rng.standard_normal((12, 4))
+    X4, s4, _ = block_gmres(lambda v: As @ v, B4, tol=1e-12)
+    assert s4 == 3 and np.allclose(As @ X4, B4, atol=1e-9)
+    _, it1, _ = gmres(lambda v: As @ v, B4[:, 0], tol=1e-12)
+    assert it1 == 12
