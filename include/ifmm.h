@@ -116,6 +116,17 @@ typedef struct {
                  (block Arnoldi, block CGS2, Cholesky QR twice); right or
                  flexible side; maxit counts block steps; columns still above
                  tol when a block loses rank finish with per-column GMRES     */
+  int matvec_precision; /* IFMM_P_FP64 (0): every product in FP64.  IFMM_P_FP32:
+                 mixed-precision iterative refinement (GMRES-IR; not in the
+                 paper): each cycle runs GMRES on A d = r, with the FMM's far
+                 field (P2M, M2M, M2L, L2L, L2P) in FP32 and its near field in
+                 FP64, until its residual estimate has fallen 1e4-fold (or
+                 below tol / 2), then x += d and r = b - A x with the FP64 FMM;
+                 a column converges when that true residual is <= tol.  At
+                 most `refine` further cycles (one that halves no column's
+                 residual ends it); IFMM_MV_FMM, right or flexible side, not
+                 with block; rel_residual is the last cycle's estimate
+                 relative to ||b||                                           */
 } ifmm_gmres_options;
 
 typedef struct {
@@ -227,6 +238,14 @@ ifmm_status ifmm_solve_prec(ifmm_ctx* ctx, const ifmm_factorization* fac, int pr
 ifmm_status fmm_matvec(ifmm_ctx* ctx, const ifmm_system* sys, int mode, const double* x,
                        double* y, int nrhs, long long ld, ifmm_stream stream);
 
+/* y = A_n x (IFMM_MV_FMM products) with prec IFMM_P_FP64 (the same as
+ * fmm_matvec) or IFMM_P_FP32: the far field (P2M, M2M, M2L, L2L, L2P) from
+ * FP32 copies of the operators in FP32 arithmetic, the near field in FP64,
+ * y = near + far added in FP64 (the inner products of GMRES-IR).  The FP32
+ * copies and plan are made on first use (allocating).  x, y as fmm_matvec. */
+ifmm_status fmm_matvec_prec(ifmm_ctx* ctx, const ifmm_system* sys, int prec, const double* x,
+                            double* y, int nrhs, long long ld, ifmm_stream stream);
+
 /* ---- allocation-free matvec --------------------------------------------------- */
 /* The paper has no counterpart to this entry point; it serves callers that
  * cannot allocate device memory while they run (a host application that owns
@@ -314,6 +333,13 @@ void ifmm_server_destroy(ifmm_server* srv);
 /* Keeps `bytes` of the budget out of later registrations, for the GMRES
  * memory of blocks (default 0; at most the budget). */
 ifmm_status ifmm_server_set_reserve(ifmm_server* srv, unsigned long long bytes);
+/* Products of the served GMRES: IFMM_P_FP64 (every product in FP64, the
+ * default) or IFMM_P_FP32 (iterative refinement, see
+ * ifmm_gmres_options.matvec_precision; at most 10 refinement cycles).  With
+ * IFMM_P_FP32 each registration also makes and admits the system's FP32
+ * far-field operators and a 32-column plan.  Call before the first
+ * ifmm_server_register (IFMM_ERR_INVALID_ARG afterwards). */
+ifmm_status ifmm_server_set_matvec_precision(ifmm_server* srv, int prec);
 /* Admits (sys, fac) if its resident device memory -- operators,
  * factorisation, solve plans and (FP32 server) the FP32 copies of the
  * factors, which this call builds -- fits what is left of hbm_budget less

@@ -45,7 +45,7 @@ class GmresReport(C.Structure):
 
 class GmresOptions(C.Structure):
     _fields_ = [("side", C.c_int), ("refine", C.c_int), ("precond_precision", C.c_int),
-                ("block", C.c_int)]
+                ("block", C.c_int), ("matvec_precision", C.c_int)]
 
 
 class SystemInfo(C.Structure):
@@ -111,6 +111,7 @@ def lib() -> C.CDLL:
         "ifmm_solve": (C.c_int, [P, P, P, P, C.c_int, C.c_longlong, P]),
         "ifmm_solve_prec": (C.c_int, [P, P, C.c_int, P, P, C.c_int, C.c_longlong, P]),
         "fmm_matvec": (C.c_int, [P, P, C.c_int, P, P, C.c_int, C.c_longlong, P]),
+        "fmm_matvec_prec": (C.c_int, [P, P, C.c_int, P, P, C.c_int, C.c_longlong, P]),
         "gmres_solve": (C.c_int, [P, P, P, C.c_int, P, P, C.c_int, C.c_longlong, C.c_double,
                                   C.c_int, C.POINTER(GmresReport), P]),
         "gmres_solve_ex": (C.c_int, [P, P, P, C.c_int, P, P, C.c_int, C.c_longlong, C.c_double,
@@ -126,6 +127,7 @@ def lib() -> C.CDLL:
                                                 C.POINTER(C.c_longlong)]),
         "ifmm_server_destroy": (None, [P]),
         "ifmm_server_set_reserve": (C.c_int, [P, C.c_ulonglong]),
+        "ifmm_server_set_matvec_precision": (C.c_int, [P, C.c_int]),
         "ifmm_server_register": (C.c_int, [P, P, P, C.c_int, C.POINTER(C.c_int)]),
         "ifmm_server_submit": (C.c_int, [P, C.c_int, P, P, C.c_int, C.c_double, C.c_int,
                                          C.POINTER(C.c_longlong)]),
@@ -291,6 +293,14 @@ def fmm_matvec(ctx, sys, mode: int, x, y, N: int, stream=None):
     _check(lib().fmm_matvec(ctx, sys, mode, px, py, k, ld, _stream(stream)), ctx)
 
 
+def fmm_matvec_prec(ctx, sys, prec: int, x, y, N: int, stream=None):
+    """y = A_n x; prec P_FP32 takes the far field in FP32 (near field FP64)."""
+    px, k, ld = _vec(x, N)
+    py, k2, _ = _vec(y, N)
+    assert k == k2
+    _check(lib().fmm_matvec_prec(ctx, sys, prec, px, py, k, ld, _stream(stream)), ctx)
+
+
 def fmm_matvec_static(ctx, sys, x, y, N: int, stream=None):
     """y = A_n x without any device allocation (library-owned static scratch)."""
     px, k, ld = _vec(x, N)
@@ -310,12 +320,13 @@ def gmres_solve(ctx, sys, fac, mode: int, b, x, N: int, tol=1e-10, maxit=500, st
 
 
 def gmres_solve_ex(ctx, sys, fac, mode: int, b, x, N: int, tol=1e-10, maxit=500,
-                   side=GMRES_RIGHT, refine=2, precond_precision=P_FP64, block=0, stream=None):
+                   side=GMRES_RIGHT, refine=2, precond_precision=P_FP64, block=0,
+                   matvec_precision=P_FP64, stream=None):
     pb, k, ld = _vec(b, N)
     px, k2, _ = _vec(x, N)
     assert k == k2
     reps = (GmresReport * k)()
-    o = GmresOptions(side, refine, precond_precision, block)
+    o = GmresOptions(side, refine, precond_precision, block, matvec_precision)
     _check(lib().gmres_solve_ex(ctx, sys, fac, mode, pb, px, k, ld, tol, maxit, C.byref(o), reps,
                                 _stream(stream)), ctx, allow=(5,))
     return list(reps)
@@ -371,6 +382,10 @@ def ifmm_server_destroy(srv):
 
 def ifmm_server_set_reserve(srv, nbytes: int):
     _scheck(lib().ifmm_server_set_reserve(srv, nbytes), srv)
+
+
+def ifmm_server_set_matvec_precision(srv, prec: int):
+    _scheck(lib().ifmm_server_set_matvec_precision(srv, prec), srv)
 
 
 def ifmm_server_register(srv, sys, fac, maxit: int = 100) -> int:

@@ -197,6 +197,19 @@ ifmm_status fmm_matvec(ifmm_ctx* ctx, const ifmm_system* sys, int mode, const do
   });
 }
 
+ifmm_status fmm_matvec_prec(ifmm_ctx* ctx, const ifmm_system* sys, int prec, const double* x,
+                            double* y, int nrhs, long long ld, ifmm_stream stream) {
+  if (!ctx || !sys || !x || !y || nrhs < 0) return IFMM_ERR_INVALID_ARG;
+  if (ld < sys->N || x == y) return IFMM_ERR_INVALID_ARG;
+  if (prec != IFMM_P_FP64 && prec != IFMM_P_FP32) return IFMM_ERR_INVALID_ARG;
+  return guard(ctx, [&] {
+    CK(cudaSetDevice(ctx->device));
+    ifmm_system* sy = const_cast<ifmm_system*>(sys);
+    if (prec == IFMM_P_FP32) system_matvec_f32far(sy, x, ld, y, ld, nrhs, st(stream));
+    else system_matvec(sy, IFMM_MV_FMM, x, ld, y, ld, nrhs, st(stream));
+  });
+}
+
 ifmm_status fmm_matvec_static(ifmm_ctx* ctx, const ifmm_system* sys, const double* x, double* y,
                               int nrhs, long long ld, ifmm_stream stream) {
   if (!ctx || !sys || !x || !y || nrhs < 0) return IFMM_ERR_INVALID_ARG;
@@ -247,6 +260,12 @@ ifmm_status gmres_solve_ex(ifmm_ctx* ctx, const ifmm_system* sys, const ifmm_fac
     if (opt->block != 0 && opt->block != 1) return IFMM_ERR_INVALID_ARG;
     if (opt->block && fac && opt->side == IFMM_GMRES_LEFT) return IFMM_ERR_INVALID_ARG;
     go.block = opt->block;
+    if (opt->matvec_precision != IFMM_P_FP64 && opt->matvec_precision != IFMM_P_FP32)
+      return IFMM_ERR_INVALID_ARG;
+    if (opt->matvec_precision == IFMM_P_FP32 &&
+        (mode != IFMM_MV_FMM || opt->block || (fac && opt->side == IFMM_GMRES_LEFT)))
+      return IFMM_ERR_INVALID_ARG;
+    go.mv_fp32 = opt->matvec_precision == IFMM_P_FP32;
   }
   ifmm_status res = IFMM_OK;
   ifmm_status g = guard(ctx, [&] {

@@ -120,6 +120,8 @@ struct ifmm_server {
   ifmm_ctx* ctx = nullptr;
   int device = 0;
   int precond_fp32 = 1;  // flexible GMRES with FP32 substitution sweeps
+  int mv_fp32 = 0;       // iterative refinement with the FMM far field in FP32
+  bool any_registered = false;
   size_t budget = 0, used = 0;  // used: resident systems (operators, factors, plans)
   size_t reserve = 0;           // kept from registrations for the GMRES blocks
   int col_cap = 32;
@@ -291,6 +293,10 @@ struct ifmm_server {
           go.side = IFMM_GMRES_FLEXIBLE;
           go.precond_fp32 = 1;
         }
+        if (mv_fp32) {
+          go.mv_fp32 = 1;
+          go.refine = 10;
+        }
         gmres_run(E.sys, E.fac, IFMM_MV_FMM, db, dx, width, N, tol, maxit, reps.data(), ws, &gws,
                   go);
         off = 0;
@@ -373,6 +379,17 @@ ifmm_status ifmm_server_create_ex(ifmm_ctx* ctx, unsigned long long hbm_budget, 
   return IFMM_OK;
 }
 
+ifmm_status ifmm_server_set_matvec_precision(ifmm_server* s, int prec) {
+  if (!s || (prec != IFMM_P_FP64 && prec != IFMM_P_FP32)) return IFMM_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> g(s->mu);
+  if (s->any_registered) {
+    s->last_error = "the matvec precision is set before the first registration";
+    return IFMM_ERR_INVALID_ARG;
+  }
+  s->mv_fp32 = prec == IFMM_P_FP32;
+  return IFMM_OK;
+}
+
 ifmm_status ifmm_server_create(ifmm_ctx* ctx, unsigned long long hbm_budget, int workers,
                                ifmm_server** out) {
   return ifmm_server_create_ex(ctx, hbm_budget, workers, IFMM_P_FP32, out);
@@ -401,8 +418,10 @@ ifmm_status ifmm_server_register(ifmm_server* s, ifmm_system* sys, ifmm_factoriz
       }
   }
   // resident device memory: operators, factorisation, its FP32 copies (built
-  // here when the server sweeps in FP32) and solve plans; the GMRES memory of
-  // a block is admitted when the block starts
+  // here when the server sweeps in FP32), solve plans, and the FMM plans and
+  // workspace for a full block (FP64, and the FP32 far field with iterative
+  // refinement), built here; the GMRES memory of a block is admitted when the
+  // block starts
   size_t bytes = sys->mem.held + fac->store.held + fac->plan_bytes();
   if (s->precond_fp32 && !fac->f32.ready) {
     size_t est = 0;
@@ -411,6 +430,11 @@ ifmm_status ifmm_server_register(ifmm_server* s, ifmm_system* sys, ifmm_factoriz
     const long long n = sys->L == 0 ? sys->N : fac->top_n;
     est += sizeof(float) * (size_t)n * n;
     bytes += est;
+  }
+  {
+    size_t fmm = ifmm::system_fmm_bytes(sys, s->col_cap);
+    if (s->mv_fp32) fmm += ifmm::system_f32far_bytes(sys, s->col_cap);
+    bytes += std::max(fmm, ifmm::system_fmm_held(sys));
   }
   std::lock_guard<std::mutex> g(s->mu);
   const size_t avail = s->budget > s->reserve ? s->budget - s->reserve : 0;
@@ -421,18 +445,26 @@ ifmm_status ifmm_server_register(ifmm_server* s, ifmm_system* sys, ifmm_factoriz
                     " remain for resident systems";
     return IFMM_ERR_BUDGET;
   }
-  if (s->precond_fp32 && !fac->f32.ready) {
+  {
+    cudaStream_t st = nullptr;
     try {
       CK(cudaSetDevice(s->device));
-      cudaStream_t st = nullptr;
       CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-      ifmm::factor_prepare_f32(fac, st);
+      if (s->precond_fp32 && !fac->f32.ready) ifmm::factor_prepare_f32(fac, st);
+      ifmm::system_prepare_fmm(sys, s->col_cap, st);
+      if (s->mv_fp32) ifmm::system_prepare_f32far(sys, s->col_cap, st);
+      CK(cudaStreamSynchronize(st));
       cudaStreamDestroy(st);
     } catch (const std::exception& e) {
+      if (st) cudaStreamDestroy(st);
       s->last_error = e.what();
       return IFMM_ERR_CUDA;
     }
   }
+  // what the system now holds (the estimate above bounded the admission)
+  bytes = std::max(bytes, sys->mem.held + fac->store.held + fac->plan_bytes() +
+                              ifmm::system_fmm_held(sys));
+  s->any_registered = true;
   s->used += bytes;
   ifmm_server::Entry e;
   e.sys = sys;

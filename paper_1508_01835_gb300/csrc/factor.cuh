@@ -116,7 +116,13 @@ struct GmresOpts {
   int refine = 2;               // restarts from x when the true residual misses tol
   int precond_fp32 = 0;         // substitution sweeps in FP32 (flexible GMRES only)
   int block = 0;                // block GMRES over the columns
+  int mv_fp32 = 0;              // iterative refinement: Arnoldi products with the far
+                                // field in FP32, true residuals in FP64
 };
+// Iterative refinement: each cycle's inner GMRES stops once its residual
+// estimate has fallen by this factor (or below tol / 2), since the FP32 far
+// field bounds what one cycle can gain.
+constexpr double IR_INNER_REDUCTION = 1e-4;
 ifmm_status gmres_run(ifmm_system* sys, ifmm_factorization* fac, int mode, const double* b,
                       double* x, int nrhs, long long ld, double tol, int maxit,
                       ifmm_gmres_report* rep, cudaStream_t s, Arena* workspace = nullptr,

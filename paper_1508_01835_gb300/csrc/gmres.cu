@@ -10,6 +10,14 @@
 // in the same maxit).  Flexible GMRES (right preconditioning that keeps
 // z_k = M^-1 v_k and forms x = Z y) is for a preconditioner applied in lower
 // precision, which is not one fixed linear operator.
+//
+// Iterative refinement (mixed-precision GMRES-IR after Carson and Higham,
+// 2018; an option, not in the paper): every cycle solves A d = r for the
+// current FP64 residual r with GMRES whose products take the FMM's far field
+// in FP32 (the near field stays FP64), to a relative reduction of
+// IR_INNER_REDUCTION; then x += d and r = b - A x with the FP64 FMM.  The
+// column converges when that true residual is <= tol ||b||; a cycle that does
+// not halve any column's residual ends the refinement.
 #include "factor.cuh"
 
 namespace ifmm {
@@ -62,6 +70,7 @@ __global__ void k_basis_combine(const double* const* __restrict__ Vtab, long lon
 struct GState {
   double beta;   // norm of this cycle's starting residual (g_0)
   double ref;    // the stopping reference: ||b|| (right) or ||M^-1 b|| (left)
+  double stop;   // this cycle stops the column once res <= stop
   double res;    // |g_{k+1}|
   int active;    // still iterating
   int iters;     // Arnoldi steps of this cycle
@@ -98,7 +107,7 @@ __global__ void k_givens(int ncols, int k, const double* __restrict__ h, int ldh
   st[c].res = fabs(gc[k + 1]);
   st[c].iters = k + 1;
   if (hnc > 0.0) inv_hn[c] = 1.0 / hnc;
-  if (st[c].res <= tol * st[c].ref || hnc == 0.0) st[c].active = 0;
+  if (st[c].res <= st[c].stop || hnc == 0.0) st[c].active = 0;
 }
 
 // y = H^-1 g (upper triangular, k_c x k_c) per column
@@ -120,16 +129,18 @@ __global__ void k_backsolve(int ncols, const double* __restrict__ H, int ldH,
 
 // Start of a cycle: beta = |r_0|; on the first cycle the stopping reference is
 // beta itself (||b|| or ||M^-1 b||), later cycles keep it.  A column already
-// within tol of its reference does not iterate.
+// within tol of its reference does not iterate.  The cycle's stop is tol ref,
+// or with iterative refinement (inner > 0) max(tol ref / 2, inner beta).
 __global__ void k_init_state(int ncols, const double* __restrict__ bn2, GState* __restrict__ st,
                              double* __restrict__ g, int ldg, double* __restrict__ inv, int first,
-                             double tol) {
+                             double tol, double inner) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= ncols) return;
   const double b = sqrt(bn2[c]);
   if (first) st[c].ref = b;
   st[c].beta = b;
   st[c].res = b;
+  st[c].stop = inner > 0.0 ? fmax(0.5 * tol * st[c].ref, inner * b) : tol * st[c].ref;
   st[c].active = b > 0.0 && !(b <= tol * st[c].ref);
   st[c].iters = 0;
   g[(long long)c * ldg] = b;
@@ -175,6 +186,15 @@ ifmm_status gmres_run(ifmm_system* sys, ifmm_factorization* fac, int mode, const
   const int side = fac ? opt.side : IFMM_GMRES_RIGHT;  // no preconditioner: plain GMRES
   if (fac && opt.precond_fp32 && side != IFMM_GMRES_FLEXIBLE)
     throw Error(IFMM_ERR_INVALID_ARG, "FP32 substitution sweeps need flexible GMRES");
+  const bool ir = opt.mv_fp32 != 0;
+  if (ir && (mode != IFMM_MV_FMM || side == IFMM_GMRES_LEFT))
+    throw Error(IFMM_ERR_INVALID_ARG,
+                "iterative refinement takes the FMM matvec and right or flexible GMRES");
+  // Arnoldi products: FP64, or with iterative refinement the FP32 far field
+  auto amv = [&](const double* in, long long ldi, double* out, long long ldo) {
+    if (ir) system_matvec_f32far(sys, in, ldi, out, ldo, nrhs, s);
+    else system_matvec(sys, mode, in, ldi, out, ldo, nrhs, s);
+  };
   // workspace: the caller's arena, rewound and reused across calls (no device
   // allocation once it has grown, so no implicit device-wide synchronisation
   // of cudaMalloc / cudaFree between concurrent solves), or a private one
@@ -208,7 +228,7 @@ ifmm_status gmres_run(ifmm_system* sys, ifmm_factorization* fac, int mode, const
   };
   std::vector<GState> hs(nrhs);
   std::vector<int> total(nrhs, 0);
-  std::vector<double> rn(nrhs);
+  std::vector<double> rn(nrhs), prev_t(nrhs, 1.0), bn(nrhs);
   int used = 0;  // Arnoldi steps so far (all cycles)
   const int cycles = 1 + std::max(0, opt.refine);
   for (int cyc = 0; cyc < cycles && used < m; cyc++) {
@@ -216,23 +236,18 @@ ifmm_status gmres_run(ifmm_system* sys, ifmm_factorization* fac, int mode, const
     const int mc = m - used;  // steps left for this cycle
     CK(cudaMemsetAsync(g, 0, sizeof(double) * (m + 1) * nrhs, s));
     CK(cudaMemsetAsync(H, 0, sizeof(double) * ((size_t)ldH * m * nrhs + 1), s));
-    // r_0: b (first cycle, x_0 = 0) or b - A x; left preconditioning applies M^-1
-    const double* r0 = b;
-    long long ldr = ld;
-    if (!first) {
-      system_matvec(sys, mode, x, ld, Wv, N, nrhs, s);
-      launch_axpby(N, nrhs, nullptr, 1.0, b, ld, 0.0, R, N, s);
-      launch_axpby(N, nrhs, nullptr, -1.0, Wv, N, 1.0, R, N, s);
-      r0 = R;
-      ldr = N;
-    }
+    // r_0: b (first cycle, x_0 = 0) or b - A x, which the previous cycle left
+    // in R; left preconditioning applies M^-1
+    const double* r0 = first ? b : R;
+    long long ldr = first ? ld : N;
     if (side == IFMM_GMRES_LEFT) {
       precond(r0, ldr, Z, N);
       r0 = Z;
       ldr = N;
     }
     launch_dots(r0, ldr, r0, ldr, N, nrhs, hn, part, s);
-    k_init_state<<<(nrhs + 63) / 64, 64, 0, s>>>(nrhs, hn, st, g, m + 1, inv, first ? 1 : 0, tol);
+    k_init_state<<<(nrhs + 63) / 64, 64, 0, s>>>(nrhs, hn, st, g, m + 1, inv, first ? 1 : 0, tol,
+                                                  ir ? IR_INNER_REDUCTION : 0.0);
     CK_LAUNCH("k_init_state");
     launch_axpby(N, nrhs, inv, 1.0, r0, ldr, 0.0, V.vec(0), ldV, s);
     CK(cudaMemcpyAsync(hs.data(), st, nrhs * sizeof(GState), cudaMemcpyDeviceToHost, s));
@@ -245,11 +260,11 @@ ifmm_status gmres_run(ifmm_system* sys, ifmm_factorization* fac, int mode, const
       if (side == IFMM_GMRES_RIGHT) {  // w = A M^-1 v_k
         if (fac) precond(vk, ldV, Z, N);
         else launch_axpby(N, nrhs, nullptr, 1.0, vk, ldV, 0.0, Z, N, s);
-        system_matvec(sys, mode, Z, N, Wv, N, nrhs, s);
+        amv(Z, N, Wv, N);
       } else if (side == IFMM_GMRES_FLEXIBLE) {  // z_k = M^-1 v_k kept, w = A z_k
         double* zk = Zb->vec(k);
         precond(vk, ldV, zk, ldV);
-        system_matvec(sys, mode, zk, ldV, Wv, N, nrhs, s);
+        amv(zk, ldV, Wv, N);
       } else {  // left: w = M^-1 A v_k
         system_matvec(sys, mode, vk, ldV, Z, N, nrhs, s);
         precond(Z, N, Wv, N);
@@ -299,35 +314,46 @@ ifmm_status gmres_run(ifmm_system* sys, ifmm_factorization* fac, int mode, const
       else launch_axpby(N, nrhs, nullptr, 1.0, Z, N, 0.0, Wv, N, s);
       launch_axpby(N, nrhs, nullptr, 1.0, Wv, N, xb, x, ld, s);
     }
-    // true residual ||b - A x|| / ||b||
+    // true residual R = b - A x (FP64; the next cycle starts from it)
     system_matvec(sys, mode, x, ld, Wv, N, nrhs, s);
-    launch_axpby(N, nrhs, nullptr, 1.0, b, ld, -1.0, Wv, N, s);
-    launch_dots(Wv, N, Wv, N, N, nrhs, hn, part, s);
+    launch_axpby(N, nrhs, nullptr, 1.0, b, ld, 0.0, R, N, s);
+    launch_axpby(N, nrhs, nullptr, -1.0, Wv, N, 1.0, R, N, s);
+    launch_dots(R, N, R, N, N, nrhs, hn, part, s);
     CK(cudaMemcpyAsync(rn.data(), hn, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
-    launch_dots(b, ld, b, ld, N, nrhs, hn, part, s);
-    std::vector<double> bn(nrhs);
-    CK(cudaMemcpyAsync(bn.data(), hn, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (first) {
+      launch_dots(b, ld, b, ld, N, nrhs, hn, part, s);
+      CK(cudaMemcpyAsync(bn.data(), hn, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
     CK(cudaMemcpyAsync(hs.data(), st, nrhs * sizeof(GState), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     // refinement: another cycle from x while a column's recomputed residual is
     // above tol although its Arnoldi estimate met it (right and flexible GMRES;
-    // left GMRES stops on the preconditioned residual, as the paper states it)
-    bool again = false;
+    // left GMRES stops on the preconditioned residual, as the paper states it);
+    // with iterative refinement while a column is above tol and some column's
+    // residual at least halved in this cycle
+    bool again = false, progress = false;
     for (int c = 0; c < nrhs; c++) {
       const double t = bn[c] > 0 ? std::sqrt(rn[c] / bn[c]) : 0.0;
       rep[c].iters = total[c];
       rep[c].rel_residual = hs[c].ref > 0 ? hs[c].res / hs[c].ref : 0.0;
       rep[c].true_rel_residual = t;
       const bool est_ok = hs[c].ref == 0.0 || hs[c].res <= tol * hs[c].ref;
-      if (side != IFMM_GMRES_LEFT && est_ok && t > tol) again = true;
+      if (ir) {
+        if (t > tol) again = true;
+        if (t <= 0.5 * prev_t[c]) progress = true;
+      } else if (side != IFMM_GMRES_LEFT && est_ok && t > tol) {
+        again = true;
+      }
+      prev_t[c] = t;
     }
-    if (!again) break;
+    if (!again || (ir && !progress)) break;
   }
   ifmm_status out = IFMM_OK;
   for (int c = 0; c < nrhs; c++) {
     const bool est_ok = hs[c].ref == 0.0 || hs[c].res <= tol * hs[c].ref;
-    const bool conv = side == IFMM_GMRES_LEFT ? est_ok
-                                              : (est_ok && rep[c].true_rel_residual <= tol);
+    const bool conv = ir ? rep[c].true_rel_residual <= tol
+                         : side == IFMM_GMRES_LEFT ? est_ok
+                                                   : (est_ok && rep[c].true_rel_residual <= tol);
     rep[c].status = conv ? IFMM_OK : IFMM_ERR_NOT_CONVERGED;
     if (!conv) out = IFMM_ERR_NOT_CONVERGED;
   }

@@ -514,4 +514,54 @@ struct NarrowTask {
 };
 void launch_narrow(Arena& ar, const std::vector<NarrowTask>& v, cudaStream_t s);
 
+// Block rows whose blocks are all nd x nd (M2M, M2L, L2L; kernels_m2l.cu):
+// tables stored as nd columns of ndp = uniform_ndp(nd) entries (zero padded),
+// coefficient vectors with ndp entries per box; y, A, x 16-byte aligned.
+template <class T>
+struct UniRow {
+  T* y;
+  long long ldy;
+  int e0, ne;
+};
+template <class T>
+struct UniEnt {
+  const T* A;
+  const T* x;
+  long long ldx;
+};
+template <class T>
+struct UniPlan {
+  const UniRow<T>* rows = nullptr;
+  const UniEnt<T>* ents = nullptr;
+  int nrows = 0, nd = 0, ndp = 0;
+  double flops = 0.0, bytes = 0.0;  // flops per right-hand side; bytes per pass
+};
+int uniform_ndp(int nd);
+bool uniform_supported(int nd);
+template <class T>
+UniPlan<T> plan_uniform(Arena& ar, const std::vector<UniRow<T>>& rows,
+                        const std::vector<UniEnt<T>>& ents, int nd, int cap, cudaStream_t s);
+template <class T>
+void launch_uniform(const UniPlan<T>& p, int nrhs, cudaStream_t s);
+// count FP64 tables nd x nd (column-major; transposed if asked) to the padded
+// layout above, in T
+template <class T>
+void launch_pad_tables(const double* src, T* dst, int count, int nd, bool transpose,
+                       cudaStream_t s);
+
+// dst (cols x rows, ld cols) = FP32 transpose of src (rows x cols, ld rows)
+struct NarrowTTask {
+  const double* src;
+  float* dst;
+  int rows, cols;
+};
+void launch_narrow_t(Arena& ar, const std::vector<NarrowTTask>& v, cudaStream_t s);
+// out64[t, c] = in[perm[t], c] and out32[t, c] = (float) in[perm[t], c]
+void launch_gather_rows_2(const long long* perm, long long N, const double* in, long long ldi,
+                          double* out64, float* out32, long long ldo, int ncols, cudaStream_t s);
+// out[perm[t], c] = in64[t, c] + (double) in32[t, c]
+void launch_scatter_rows_add(const long long* perm, long long N, const double* in64,
+                             const float* in32, long long ldi, double* out, long long ldo,
+                             int ncols, cudaStream_t s);
+
 }  // namespace ifmm

@@ -236,14 +236,15 @@ __global__ void __launch_bounds__(256) k_spmm_reduce(const SpRow* __restrict__ r
                                                      long long pld, int c0, int nb) {
   const SpRed D = reds[blockIdx.x];
   const SpRow R = rows[D.row];
-  for (int c = 0; c < nb; c++)
-    for (int r = threadIdx.x; r < R.m; r += blockDim.x) {
-      const double* pp = part + D.base + r + (long long)c * pld;
-      double v = 0.0;
-      for (int j = 0; j < D.nj; j++) v += pp[(long long)j * R.m];
-      double* y = R.y + (long long)(c0 + c) * R.ldy + r;
-      *y = (R.beta == 0.0) ? v : fma(R.beta, *y, v);
-    }
+  // every thread takes (row, column) pairs: all threads busy for short rows
+  for (int e = threadIdx.x; e < R.m * nb; e += blockDim.x) {
+    const int r = e % R.m, c = e / R.m;
+    const double* pp = part + D.base + r + (long long)c * pld;
+    double v = 0.0;
+    for (int j = 0; j < D.nj; j++) v += pp[(long long)j * R.m];
+    double* y = R.y + (long long)(c0 + c) * R.ldy + r;
+    *y = (R.beta == 0.0) ? v : fma(R.beta, *y, v);
+  }
 }
 
 // Job split shared by the FP64 and FP32 products: about four jobs per SM, no
@@ -416,14 +417,14 @@ __global__ void __launch_bounds__(256) k_spmm_f32_reduce(const SpRowF* __restric
                                                          long long pld, int c0, int nb) {
   const SpRed D = reds[blockIdx.x];
   const SpRowF R = rows[D.row];
-  for (int c = 0; c < nb; c++)
-    for (int r = threadIdx.x; r < R.m; r += blockDim.x) {
-      const float* pp = part + D.base + r + (long long)c * pld;
-      float v = 0.0f;
-      for (int j = 0; j < D.nj; j++) v += pp[(long long)j * R.m];
-      float* y = R.y + (long long)(c0 + c) * R.ldy + r;
-      *y = (R.beta == 0.0f) ? v : fmaf(R.beta, *y, v);
-    }
+  for (int e = threadIdx.x; e < R.m * nb; e += blockDim.x) {
+    const int r = e % R.m, c = e / R.m;
+    const float* pp = part + D.base + r + (long long)c * pld;
+    float v = 0.0f;
+    for (int j = 0; j < D.nj; j++) v += pp[(long long)j * R.m];
+    float* y = R.y + (long long)(c0 + c) * R.ldy + r;
+    *y = (R.beta == 0.0f) ? v : fmaf(R.beta, *y, v);
+  }
 }
 
 SpmmPlanF plan_spmm_f32(Arena& ar, const std::vector<SpRowF>& rows,
@@ -531,6 +532,73 @@ void launch_narrow(Arena& ar, const std::vector<NarrowTask>& v, cudaStream_t s) 
   if (keep.empty()) return;
   k_narrow<<<(int)keep.size(), 256, 0, s>>>(upload(ar, keep, s));
   CK_LAUNCH("k_narrow");
+}
+
+__global__ void k_narrow_t(const NarrowTTask* __restrict__ t) {
+  const NarrowTTask T = t[blockIdx.x];
+  const long long n = (long long)T.rows * T.cols;
+  for (long long e = threadIdx.x; e < n; e += blockDim.x) {
+    const int c = (int)(e % T.cols), r = (int)(e / T.cols);  // dst[c + r * cols]
+    T.dst[e] = (float)T.src[r + (long long)c * T.rows];
+  }
+}
+void launch_narrow_t(Arena& ar, const std::vector<NarrowTTask>& v, cudaStream_t s) {
+  std::vector<NarrowTTask> keep;
+  for (const NarrowTTask& t : v)
+    if (t.rows > 0 && t.cols > 0) {
+      const size_t n = (size_t)t.rows * t.cols;
+      Ranges::check(t.src, sizeof(double) * n, "narrow_t src");
+      Ranges::check(t.dst, sizeof(float) * n, "narrow_t dst");
+      keep.push_back(t);
+    }
+  for (size_t b = 0; b < keep.size(); b += 65535) {
+    const size_t e = std::min(keep.size(), b + 65535);
+    std::vector<NarrowTTask> part(keep.begin() + b, keep.begin() + e);
+    k_narrow_t<<<(int)part.size(), 128, 0, s>>>(upload(ar, part, s));
+    CK_LAUNCH("k_narrow_t");
+  }
+}
+
+__global__ void k_gather_rows_2(const long long* __restrict__ perm, long long N,
+                                const double* __restrict__ in, long long ldi,
+                                double* __restrict__ out64, float* __restrict__ out32,
+                                long long ldo, int ncols) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N) return;
+  const long long src = perm[t];
+  for (int c = 0; c < ncols; c++) {
+    const double v = in[src + c * ldi];
+    out64[t + c * ldo] = v;
+    out32[t + c * ldo] = (float)v;
+  }
+}
+void launch_gather_rows_2(const long long* perm, long long N, const double* in, long long ldi,
+                          double* out64, float* out32, long long ldo, int ncols, cudaStream_t s) {
+  if (N <= 0 || ncols <= 0) return;
+  Prof p("k_gather_rows_2", 0.0, (8.0 + 8.0 + 8.0 + 4.0) * N * ncols, s);
+  k_gather_rows_2<<<(int)((N + 255) / 256), 256, 0, s>>>(perm, N, in, ldi, out64, out32, ldo,
+                                                         ncols);
+  CK_LAUNCH("k_gather_rows_2");
+}
+
+__global__ void k_scatter_rows_add(const long long* __restrict__ perm, long long N,
+                                   const double* __restrict__ in64, const float* __restrict__ in32,
+                                   long long ldi, double* __restrict__ out, long long ldo,
+                                   int ncols) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N) return;
+  const long long dst = perm[t];
+  for (int c = 0; c < ncols; c++)
+    out[dst + c * ldo] = in64[t + c * ldi] + (double)in32[t + c * ldi];
+}
+void launch_scatter_rows_add(const long long* perm, long long N, const double* in64,
+                             const float* in32, long long ldi, double* out, long long ldo,
+                             int ncols, cudaStream_t s) {
+  if (N <= 0 || ncols <= 0) return;
+  Prof p("k_scatter_rows_add", 0.0, (8.0 + 8.0 + 4.0 + 8.0) * N * ncols, s);
+  k_scatter_rows_add<<<(int)((N + 255) / 256), 256, 0, s>>>(perm, N, in64, in32, ldi, out, ldo,
+                                                            ncols);
+  CK_LAUNCH("k_scatter_rows_add");
 }
 
 void launch_spmm(const SpmmPlan& p, int nrhs, cudaStream_t s) {

@@ -219,68 +219,157 @@ ifmm_system* system_create(ifmm_ctx* ctx, const double* pts, bool host, long lon
 // ---------------------------------------------------------------------------
 // FMM matvec plan: P2M, M2M per level, M2L + L2L per level, L2P + P2P
 // ---------------------------------------------------------------------------
+// The nd x nd translations (M2M, M2L + L2L) run as uniform block rows when
+// nd <= 64 (coefficient vectors then hold uniform_ndp(nd) entries per box);
+// P2M, L2P and the near field as general block-row products.
+static void make_padded_tables(ifmm_system* sys, ChebOps& ops, cudaStream_t s) {
+  if (ops.transfer_pad) return;
+  const int nd = ops.nd, dim = sys->dim, ndp = uniform_ndp(nd);
+  const int nt = 1 << dim;
+  int no = 1;
+  for (int d = 0; d < dim; d++) no *= 7;
+  ops.transfer_pad = sys->mem.alloc<double>((size_t)nt * nd * ndp);
+  ops.transferT_pad = sys->mem.alloc<double>((size_t)nt * nd * ndp);
+  launch_pad_tables<double>(ops.transfer, ops.transfer_pad, nt, nd, false, s);
+  launch_pad_tables<double>(ops.transfer, ops.transferT_pad, nt, nd, true, s);
+  ops.m2l_pad.assign(sys->L + 1, nullptr);
+  for (int l = 2; l <= sys->L; l++) {
+    ops.m2l_pad[l] = sys->mem.alloc<double>((size_t)no * nd * ndp);
+    launch_pad_tables<double>(ops.m2l[l], ops.m2l_pad[l], no, nd, false, s);
+  }
+}
+
 static void build_fmm_plan(ifmm_system* sys, int cap, cudaStream_t s) {
   sys->fmm_graph.reset();
   sys->fmm_plan.phases.clear();
   sys->fmm_plan.mem.reset();
+  sys->fmm_uni.clear();
+  sys->fmm_order.clear();
   sys->fmm_ws.release();
   sys->fmm_cap = cap;
-  const ChebOps& ops = sys->mv();
+  ChebOps& ops = sys->same_ops ? sys->ops_f : sys->ops_mv;
   const int nd = ops.nd, L = sys->L, dim = sys->dim;
+  const bool uni = uniform_supported(nd);
+  const int ndp = uni ? uniform_ndp(nd) : nd;
+  if (uni) make_padded_tables(sys, ops, s);
   const long long N = sys->N;
   sys->fmm_x = sys->fmm_ws.alloc<double>((size_t)N * cap);
   sys->fmm_y = sys->fmm_ws.alloc<double>((size_t)N * cap);
   std::vector<double*> mult(L + 1, nullptr), loc(L + 1, nullptr);
   std::vector<long long> ldl(L + 1, 0);
   for (int l = 2; l <= L; l++) {
-    ldl[l] = (long long)sys->lv[l].nb * nd;
+    ldl[l] = (long long)sys->lv[l].nb * ndp;
     mult[l] = sys->fmm_ws.alloc<double>((size_t)ldl[l] * cap);
     loc[l] = sys->fmm_ws.alloc<double>((size_t)ldl[l] * cap);
+    // padding rows are staged by the uniform kernel (never multiplied): keep them finite
+    CK(cudaMemsetAsync(mult[l], 0, sizeof(double) * (size_t)ldl[l] * cap, s));
+    CK(cudaMemsetAsync(loc[l], 0, sizeof(double) * (size_t)ldl[l] * cap, s));
   }
   const LevelTopo& leaf = sys->lv[L];
   SpBuild b;
+  auto flush = [&] {
+    if (b.rows.empty()) return;
+    b.flush(sys->fmm_plan, s, cap);
+    sys->fmm_order.push_back(0);
+  };
+  std::vector<UniRow<double>> urows;
+  std::vector<UniEnt<double>> uents;
+  auto urow = [&](double* y, long long ldy) { urows.push_back({y, ldy, (int)uents.size(), 0}); };
+  auto uent = [&](const double* A, const double* x, long long ldx) {
+    uents.push_back({A, x, ldx});
+    urows.back().ne++;
+  };
+  auto uflush = [&] {
+    sys->fmm_uni.push_back(plan_uniform<double>(sys->fmm_plan.mem, urows, uents, nd, cap, s));
+    sys->fmm_order.push_back(1);
+    urows.clear();
+    uents.clear();
+  };
   for (int i = 0; i < leaf.nb; i++) {  // P2M
     const int m = leaf.p1[i] - leaf.p0[i];
-    b.row(mult[L] + (long long)i * nd, ldl[L], nd);
+    b.row(mult[L] + (long long)i * ndp, ldl[L], nd);
     b.ent(ops.leafU + ops.uoff[i], m, m, 1, sys->fmm_x + leaf.p0[i], N);
   }
-  b.flush(sys->fmm_plan, s, cap);
+  flush();
   for (int l = L - 1; l >= 2; l--) {  // M2M
     const LevelTopo& v = sys->lv[l];
     const LevelTopo& c = sys->lv[l + 1];
     for (int p = 0; p < v.nb; p++) {
-      b.row(mult[l] + (long long)p * nd, ldl[l], nd);
-      for (int ch = v.cb[p]; ch < v.ce[p]; ch++)
-        b.ent(ops.transfer + (size_t)c.child_pos(ch, dim) * nd * nd, nd, nd, 1,
-              mult[l + 1] + (long long)ch * nd, ldl[l + 1]);
+      if (uni) urow(mult[l] + (long long)p * ndp, ldl[l]);
+      else b.row(mult[l] + (long long)p * ndp, ldl[l], nd);
+      for (int ch = v.cb[p]; ch < v.ce[p]; ch++) {
+        const size_t t = (size_t)c.child_pos(ch, dim) * nd;
+        if (uni) uent(ops.transferT_pad + t * ndp, mult[l + 1] + (long long)ch * ndp, ldl[l + 1]);
+        else b.ent(ops.transfer + t * nd, nd, nd, 1, mult[l + 1] + (long long)ch * ndp, ldl[l + 1]);
+      }
     }
-    b.flush(sys->fmm_plan, s, cap);
+    if (uni) uflush();
+    else flush();
   }
   for (int l = 2; l <= L; l++) {  // M2L + L2L
     const LevelTopo& v = sys->lv[l];
     for (int i = 0; i < v.nb; i++) {
-      b.row(loc[l] + (long long)i * nd, ldl[l], nd);
+      if (uni) urow(loc[l] + (long long)i * ndp, ldl[l]);
+      else b.row(loc[l] + (long long)i * ndp, ldl[l], nd);
       for (int k = v.far_ptr[i]; k < v.far_ptr[i + 1]; k++) {
         const int q = v.far[k];
-        b.ent(ops.m2l[l] + (size_t)v.m2l_offset(i, q, dim) * nd * nd, nd, nd, 0,
-              mult[l] + (long long)q * nd, ldl[l]);
+        const size_t t = (size_t)v.m2l_offset(i, q, dim) * nd;
+        if (uni) uent(ops.m2l_pad[l] + t * ndp, mult[l] + (long long)q * ndp, ldl[l]);
+        else b.ent(ops.m2l[l] + t * nd, nd, nd, 0, mult[l] + (long long)q * ndp, ldl[l]);
       }
-      if (l > 2)
-        b.ent(ops.transfer + (size_t)v.child_pos(i, dim) * nd * nd, nd, nd, 0,
-              loc[l - 1] + (long long)v.parent[i] * nd, ldl[l - 1]);
+      if (l > 2) {
+        const size_t t = (size_t)v.child_pos(i, dim) * nd;
+        const double* xp = loc[l - 1] + (long long)v.parent[i] * ndp;
+        if (uni) uent(ops.transfer_pad + t * ndp, xp, ldl[l - 1]);
+        else b.ent(ops.transfer + t * nd, nd, nd, 0, xp, ldl[l - 1]);
+      }
     }
-    b.flush(sys->fmm_plan, s, cap);
+    if (uni) uflush();
+    else flush();
   }
   for (int i = 0; i < leaf.nb; i++) {  // L2P + P2P
     const int m = leaf.p1[i] - leaf.p0[i];
     b.row(sys->fmm_y + leaf.p0[i], N, m);
-    b.ent(ops.leafU + ops.uoff[i], m, nd, 0, loc[L] + (long long)i * nd, ldl[L]);
+    b.ent(ops.leafU + ops.uoff[i], m, nd, 0, loc[L] + (long long)i * ndp, ldl[L]);
     for (int k = leaf.nbr_ptr[i]; k < leaf.nbr_ptr[i + 1]; k++) {
       const int j = leaf.nbr[k];
       b.ent(sys->p2p + sys->p2p_off[k], m, leaf.p1[j] - leaf.p0[j], 0, sys->fmm_x + leaf.p0[j], N);
     }
   }
-  b.flush(sys->fmm_plan, s, cap);
+  flush();
+  CK(cudaStreamSynchronize(s));
+}
+
+static void run_fmm_phases(const ifmm_system* sys, int nrhs, cudaStream_t s) {
+  size_t a = 0, u = 0;
+  for (int kind : sys->fmm_order) {
+    if (kind == 0) launch_spmm(sys->fmm_plan.phases[a++], nrhs, s);
+    else launch_uniform<double>(sys->fmm_uni[u++], nrhs, s);
+  }
+}
+
+size_t system_fmm_bytes(const ifmm_system* sys, int cap) {
+  if (sys->L == 0) return 0;
+  const int nd = sys->mv().nd;
+  const int ndp = uniform_supported(nd) ? uniform_ndp(nd) : nd;
+  size_t b = 2 * sizeof(double) * (size_t)sys->N * cap;  // x, y in tree order
+  size_t ents = 0;
+  for (int l = 2; l <= sys->L; l++) {
+    b += 2 * sizeof(double) * (size_t)sys->lv[l].nb * ndp * cap;  // multipoles, locals
+    ents += sys->lv[l].far.size() + 2 * (size_t)sys->lv[l].nb;
+  }
+  ents += sys->lv[sys->L].nbr.size();
+  return b + 64 * ents + (size_t(16) << 20);
+}
+
+size_t system_fmm_held(const ifmm_system* sys) {
+  return sys->fmm_ws.held + sys->fmm_plan.mem.held + sys->f32.ops.held + sys->f32.ws.held;
+}
+
+void system_prepare_fmm(ifmm_system* sys, int cap, cudaStream_t s) {
+  if (sys->L == 0 || cap <= sys->fmm_cap) return;
+  CK(cudaStreamSynchronize(s));
+  build_fmm_plan(sys, cap, s);
 }
 
 void system_matvec(ifmm_system* sys, int mode, const double* x, long long ldx, double* y,
@@ -296,8 +385,240 @@ void system_matvec(ifmm_system* sys, int mode, const double* x, long long ldx, d
   }
   launch_gather_rows(sys->perm, sys->N, x, ldx, sys->fmm_x, sys->N, nrhs, s);
   run_graph(sys->fmm_graph, nrhs, "graph:fmm_matvec", s,
-            [&](cudaStream_t gs) { sys->fmm_plan.run(nrhs, gs); });
+            [&](cudaStream_t gs) { run_fmm_phases(sys, nrhs, gs); });
   launch_scatter_rows(sys->perm, sys->N, sys->fmm_y, sys->N, y, ldy, nrhs, s);
+}
+
+// ---------------------------------------------------------------------------
+// FMM matvec with the far field in FP32.  FP32 copies of the operators of the
+// matvec's Chebyshev order (leaf U_i and its transpose, the 2^D transfers and
+// their transposes, the M2L tables); P2M, M2M, M2L + L2L and L2P run in FP32
+// on FP32 coefficients, the near field as FP64 products; y = near + far,
+// added in FP64 in the scatter back to user order.
+// ---------------------------------------------------------------------------
+static void build_f32_ops(ifmm_system* sys, cudaStream_t s) {
+  Fmm32& f = sys->f32;
+  if (f.leafU) return;
+  const ChebOps& ops = sys->mv();
+  const int nd = ops.nd, dim = sys->dim, L = sys->L;
+  const int nt = 1 << dim;
+  int no = 1;
+  for (int d = 0; d < dim; d++) no *= 7;
+  const LevelTopo& leaf = sys->lv[L];
+  long long tot = 0;
+  for (int i = 0; i < leaf.nb; i++) tot += (long long)(leaf.p1[i] - leaf.p0[i]) * nd;
+  // tables: the uniform kernel's padded layout (nd <= 64) or plain nd x nd
+  const bool uni = uniform_supported(nd);
+  const int ndp = uni ? uniform_ndp(nd) : nd;
+  f.leafU = f.ops.alloc<float>((size_t)tot);
+  f.leafUT = f.ops.alloc<float>((size_t)tot);
+  f.transfer = f.ops.alloc<float>((size_t)nt * nd * ndp);
+  f.transferT = f.ops.alloc<float>((size_t)nt * nd * ndp);
+  f.m2l.assign(L + 1, nullptr);
+  for (int l = 2; l <= L; l++) f.m2l[l] = f.ops.alloc<float>((size_t)no * nd * ndp);
+  std::vector<NarrowTask> nt1{{ops.leafU, f.leafU, tot}};
+  std::vector<NarrowTTask> nt2;
+  for (int i = 0; i < leaf.nb; i++)
+    nt2.push_back({ops.leafU + ops.uoff[i], f.leafUT + ops.uoff[i], leaf.p1[i] - leaf.p0[i], nd});
+  if (uni) {
+    launch_pad_tables<float>(ops.transfer, f.transfer, nt, nd, false, s);
+    launch_pad_tables<float>(ops.transfer, f.transferT, nt, nd, true, s);
+    for (int l = 2; l <= L; l++) launch_pad_tables<float>(ops.m2l[l], f.m2l[l], no, nd, false, s);
+  } else {
+    nt1.push_back({ops.transfer, f.transfer, (long long)nt * nd * nd});
+    for (int l = 2; l <= L; l++) nt1.push_back({ops.m2l[l], f.m2l[l], (long long)no * nd * nd});
+    for (int c = 0; c < nt; c++)
+      nt2.push_back({ops.transfer + (size_t)c * nd * nd, f.transferT + (size_t)c * nd * nd, nd, nd});
+  }
+  Arena tmp;
+  launch_narrow(tmp, nt1, s);
+  launch_narrow_t(tmp, nt2, s);
+  CK(cudaStreamSynchronize(s));
+}
+
+struct F32Sizes {
+  size_t vec = 0;              // x64, y64, x32, y32
+  std::vector<long long> ldl;  // per depth: nb * ndp
+};
+static F32Sizes f32_sizes(const ifmm_system* sys, int cap) {
+  F32Sizes z;
+  const int nd = sys->mv().nd;
+  const int ndp = uniform_supported(nd) ? uniform_ndp(nd) : nd;
+  z.ldl.assign(sys->L + 1, 0);
+  for (int l = 2; l <= sys->L; l++) z.ldl[l] = (long long)sys->lv[l].nb * ndp;
+  z.vec = (size_t)sys->N * cap;
+  return z;
+}
+
+static void build_f32_plan(ifmm_system* sys, int cap, cudaStream_t s) {
+  build_f32_ops(sys, s);
+  Fmm32& f = sys->f32;
+  f.graph.reset();
+  f.far.clear();
+  f.far_uni.clear();
+  f.order.clear();
+  f.near.clear();
+  f.ws.release();
+  f.cap = cap;
+  const ChebOps& ops = sys->mv();
+  const int nd = ops.nd, L = sys->L, dim = sys->dim;
+  const bool uni = uniform_supported(nd);
+  const int ndp = uni ? uniform_ndp(nd) : nd;
+  const long long N = sys->N;
+  const F32Sizes z = f32_sizes(sys, cap);
+  f.x64 = f.ws.alloc<double>(z.vec);
+  f.y64 = f.ws.alloc<double>(z.vec);
+  f.x32 = f.ws.alloc<float>(z.vec);
+  f.y32 = f.ws.alloc<float>(z.vec);
+  std::vector<float*> mult(L + 1, nullptr), loc(L + 1, nullptr);
+  for (int l = 2; l <= L; l++) {
+    mult[l] = f.ws.alloc<float>((size_t)z.ldl[l] * cap);
+    loc[l] = f.ws.alloc<float>((size_t)z.ldl[l] * cap);
+    CK(cudaMemsetAsync(mult[l], 0, sizeof(float) * (size_t)z.ldl[l] * cap, s));
+    CK(cudaMemsetAsync(loc[l], 0, sizeof(float) * (size_t)z.ldl[l] * cap, s));
+  }
+  const std::vector<long long>& ldl = z.ldl;
+  std::vector<SpRowF> rows;
+  std::vector<SpEntF> ents;
+  auto row = [&](float* y, long long ldy, int m) {
+    rows.push_back({y, ldy, m, (int)ents.size(), 0, 0.0f});
+  };
+  auto ent = [&](const float* A, int lda, int k, const float* x, long long ldx) {
+    ents.push_back({A, x, ldx, lda, k, 1.0f});
+    rows.back().ne++;
+  };
+  auto flush = [&] {
+    if (rows.empty()) return;
+    f.far.push_back(plan_spmm_f32(f.ws, rows, ents, cap, s));
+    f.order.push_back(0);
+    rows.clear();
+    ents.clear();
+  };
+  std::vector<UniRow<float>> urows;
+  std::vector<UniEnt<float>> uents;
+  auto urow = [&](float* y, long long ldy) { urows.push_back({y, ldy, (int)uents.size(), 0}); };
+  auto uent = [&](const float* A, const float* x, long long ldx) {
+    uents.push_back({A, x, ldx});
+    urows.back().ne++;
+  };
+  auto uflush = [&] {
+    f.far_uni.push_back(plan_uniform<float>(f.ws, urows, uents, nd, cap, s));
+    f.order.push_back(1);
+    urows.clear();
+    uents.clear();
+  };
+  // a row of nd x nd blocks: the uniform kernel, or general products from the
+  // plain tables
+  auto trow = [&](float* y, long long ldy) {
+    if (uni) urow(y, ldy);
+    else row(y, ldy, nd);
+  };
+  auto tent = [&](const float* table, size_t t, const float* x, long long ldx) {
+    if (uni) uent(table + t * nd * ndp, x, ldx);
+    else ent(table + t * nd * nd, nd, nd, x, ldx);
+  };
+  auto tflush = [&] {
+    if (uni) uflush();
+    else flush();
+  };
+  const LevelTopo& leaf = sys->lv[L];
+  for (int i = 0; i < leaf.nb; i++) {  // P2M: mult_i = U_i^T x_i
+    const int m = leaf.p1[i] - leaf.p0[i];
+    row(mult[L] + (long long)i * ndp, ldl[L], nd);
+    ent(f.leafUT + ops.uoff[i], nd, m, f.x32 + leaf.p0[i], N);
+  }
+  flush();
+  for (int l = L - 1; l >= 2; l--) {  // M2M: mult_p = sum_c T_c^T mult_c
+    const LevelTopo& v = sys->lv[l];
+    const LevelTopo& c = sys->lv[l + 1];
+    for (int p = 0; p < v.nb; p++) {
+      trow(mult[l] + (long long)p * ndp, ldl[l]);
+      for (int ch = v.cb[p]; ch < v.ce[p]; ch++)
+        tent(f.transferT, (size_t)c.child_pos(ch, dim), mult[l + 1] + (long long)ch * ndp,
+             ldl[l + 1]);
+    }
+    tflush();
+  }
+  for (int l = 2; l <= L; l++) {  // M2L + L2L
+    const LevelTopo& v = sys->lv[l];
+    for (int i = 0; i < v.nb; i++) {
+      trow(loc[l] + (long long)i * ndp, ldl[l]);
+      for (int k = v.far_ptr[i]; k < v.far_ptr[i + 1]; k++) {
+        const int q = v.far[k];
+        tent(f.m2l[l], (size_t)v.m2l_offset(i, q, dim), mult[l] + (long long)q * ndp, ldl[l]);
+      }
+      if (l > 2)
+        tent(f.transfer, (size_t)v.child_pos(i, dim), loc[l - 1] + (long long)v.parent[i] * ndp,
+             ldl[l - 1]);
+    }
+    tflush();
+  }
+  for (int i = 0; i < leaf.nb; i++) {  // L2P: y_i = U_i loc_i
+    const int m = leaf.p1[i] - leaf.p0[i];
+    row(f.y32 + leaf.p0[i], N, m);
+    ent(f.leafU + ops.uoff[i], m, nd, loc[L] + (long long)i * ndp, ldl[L]);
+  }
+  flush();
+  SpBuild b;  // near field, FP64
+  for (int i = 0; i < leaf.nb; i++) {
+    const int m = leaf.p1[i] - leaf.p0[i];
+    b.row(f.y64 + leaf.p0[i], N, m);
+    for (int k = leaf.nbr_ptr[i]; k < leaf.nbr_ptr[i + 1]; k++) {
+      const int j = leaf.nbr[k];
+      b.ent(sys->p2p + sys->p2p_off[k], m, leaf.p1[j] - leaf.p0[j], 0, f.x64 + leaf.p0[j], N);
+    }
+  }
+  f.near.push_back(plan_spmm(f.ws, b.rows, b.ents, cap, s));
+  CK(cudaStreamSynchronize(s));
+}
+
+size_t system_f32far_bytes(const ifmm_system* sys, int cap) {
+  if (sys->L == 0) return 0;
+  const int nd = sys->mv().nd, dim = sys->dim;
+  int no = 1;
+  for (int d = 0; d < dim; d++) no *= 7;
+  const F32Sizes z = f32_sizes(sys, cap);
+  const int ndp = uniform_supported(nd) ? uniform_ndp(nd) : nd;
+  size_t b = 2 * sizeof(float) * (size_t)sys->N * nd;              // U, U^T
+  b += 2 * sizeof(float) * ((size_t)(1 << dim) * nd * ndp);         // transfers
+  b += sizeof(float) * (size_t)(sys->L - 1) * no * nd * ndp;         // M2L tables
+  b += (2 * sizeof(double) + 2 * sizeof(float)) * z.vec;            // x, y
+  for (int l = 2; l <= sys->L; l++) b += 2 * sizeof(float) * (size_t)z.ldl[l] * cap;
+  // plan descriptors and split-K partial sums: about 64 bytes per block entry
+  size_t ents = 0;
+  for (int l = 2; l <= sys->L; l++) ents += sys->lv[l].far.size() + 2 * (size_t)sys->lv[l].nb;
+  ents += sys->lv[sys->L].nbr.size();
+  return b + 64 * ents + (size_t(16) << 20);
+}
+
+void system_prepare_f32far(ifmm_system* sys, int cap, cudaStream_t s) {
+  if (sys->L == 0 || cap <= sys->f32.cap) return;
+  CK(cudaStreamSynchronize(s));
+  build_f32_plan(sys, cap, s);
+}
+
+void system_matvec_f32far(ifmm_system* sys, const double* x, long long ldx, double* y,
+                          long long ldy, int nrhs, cudaStream_t s) {
+  if (nrhs <= 0) return;
+  if (sys->L == 0) {
+    system_matvec(sys, IFMM_MV_FMM, x, ldx, y, ldy, nrhs, s);
+    return;
+  }
+  Fmm32& f = sys->f32;
+  if (nrhs > f.cap) {
+    CK(cudaStreamSynchronize(s));
+    build_f32_plan(sys, std::max(nrhs, 4), s);
+  }
+  launch_gather_rows_2(sys->perm, sys->N, x, ldx, f.x64, f.x32, sys->N, nrhs, s);
+  run_graph(f.graph, nrhs, "graph:fmm_matvec_f32far", s, [&](cudaStream_t gs) {
+    size_t a = 0, u = 0;
+    for (int kind : f.order) {
+      if (kind == 0) launch_spmm_f32(f.far[a++], nrhs, gs);
+      else launch_uniform<float>(f.far_uni[u++], nrhs, gs);
+    }
+    for (const SpmmPlan& p : f.near) launch_spmm(p, nrhs, gs);
+  });
+  launch_scatter_rows_add(sys->perm, sys->N, f.y64, f.y32, sys->N, y, ldy, nrhs, s);
 }
 
 // ---------------------------------------------------------------------------

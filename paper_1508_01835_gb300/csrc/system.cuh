@@ -60,6 +60,11 @@ struct ChebOps {
   std::vector<long long> uoff;
   double* transfer = nullptr;       // 2^D blocks nd x nd
   std::vector<double*> m2l;         // per depth: 7^D blocks nd x nd (depth >= 2)
+  // the same tables in the padded column layout of the uniform block-row
+  // kernel (nd columns of uniform_ndp(nd) entries), made with the FMM plan
+  double* transfer_pad = nullptr;   // L2L
+  double* transferT_pad = nullptr;  // M2M (transposed)
+  std::vector<double*> m2l_pad;
 };
 
 // Device copies of the lists the allocation-free matvec reads (built once when
@@ -88,6 +93,29 @@ struct SpPlan {
     for (const SpmmPlan& p : phases) launch_spmm(p, nrhs, s);
   }
 };
+// FMM matvec with the far field in FP32: P2M, M2M, M2L, L2L and L2P read
+// FP32 copies of the operators (P2M reads stored transposes of U_i, M2M the
+// transposed transfers) and FP32 coefficients; the near field (P2P) stays
+// FP64.  Used for the inner iterations of GMRES with iterative refinement,
+// whose residuals are FP64.
+struct Fmm32 {
+  Arena ops;                  // operator copies, kept once made
+  Arena ws;                   // plans and workspace, rebuilt when nrhs grows
+  float* leafU = nullptr;     // per leaf m_i x nd (offsets as ChebOps::uoff)
+  float* leafUT = nullptr;    // per leaf nd x m_i
+  float* transfer = nullptr;  // 2^D blocks nd x nd (padded layout when uniform)
+  float* transferT = nullptr;
+  std::vector<float*> m2l;    // per depth: 7^D blocks
+  std::vector<SpmmPlanF> far;           // P2M, L2P (and M2M, M2L/L2L when nd > 64)
+  std::vector<UniPlan<float>> far_uni;  // M2M, M2L + L2L (nd <= 64)
+  std::vector<int> order;               // phase sequence: 0 next far, 1 next far_uni
+  std::vector<SpmmPlan> near;
+  double *x64 = nullptr, *y64 = nullptr;  // tree order
+  float *x32 = nullptr, *y32 = nullptr;
+  int cap = 0;
+  GraphCache graph;
+};
+
 struct SpBuild {
   std::vector<SpRow> rows;
   std::vector<SpEnt> ents;
@@ -132,9 +160,12 @@ struct ifmm_system {
   // FMM matvec plan and its workspace (grown on demand)
   ifmm::Arena fmm_ws;
   ifmm::SpPlan fmm_plan;
+  std::vector<ifmm::UniPlan<double>> fmm_uni;  // M2M, M2L + L2L phases (nd <= 64)
+  std::vector<int> fmm_order;                  // 0: next fmm_plan phase, 1: next fmm_uni
   ifmm::GraphCache fmm_graph;  // fmm_plan.run as one graph
   int fmm_cap = 0;
   double *fmm_x = nullptr, *fmm_y = nullptr;
+  ifmm::Fmm32 f32;                           // FP32 far field (made on first use)
   std::vector<ifmm::StaticLevelLists> static_lv;  // per depth 2..L (fmm_matvec_static)
   ifmm::StaticLeafLists static_leaf;
   double sigma0 = std::numeric_limits<double>::quiet_NaN();
@@ -147,6 +178,19 @@ ifmm_system* system_create(ifmm_ctx* ctx, const double* pts, bool host, long lon
                            const ifmm_kernel* k, const ifmm_options* opt, cudaStream_t s);
 void system_matvec(ifmm_system* sys, int mode, const double* x, long long ldx, double* y,
                    long long ldy, int nrhs, cudaStream_t s);
+// FP64 FMM plan and workspace: bytes for `cap` columns (estimate), bytes held
+// by the FMM plans of both precisions, and building the plan for `cap` now
+size_t system_fmm_bytes(const ifmm_system* sys, int cap);
+size_t system_fmm_held(const ifmm_system* sys);
+void system_prepare_fmm(ifmm_system* sys, int cap, cudaStream_t s);
+// y = A_n x with the far field in FP32 (see Fmm32); the FP64 product when the
+// system has no tree.  Builds the FP32 operators and plan on first use.
+void system_matvec_f32far(ifmm_system* sys, const double* x, long long ldx, double* y,
+                          long long ldy, int nrhs, cudaStream_t s);
+// makes the FP32 far-field operators and a plan for `cap` columns now
+void system_prepare_f32far(ifmm_system* sys, int cap, cudaStream_t s);
+// device bytes of the FP32 far-field operators and plan for `cap` columns
+size_t system_f32far_bytes(const ifmm_system* sys, int cap);
 double system_sigma0(ifmm_system* sys, cudaStream_t s, int* iters);
 void system_matvec_static(ifmm_system* sys, const double* x, double* y, int nrhs, long long ld,
                           int device, cudaStream_t s);

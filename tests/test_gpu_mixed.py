@@ -235,3 +235,118 @@ def test_bf16_schur_products_at_loose_eps(ctx):
         finally:
             ifmm.ifmm_system_destroy(sys)
     print(f"eps 1e-3: GMRES iterations FP64 Schur {its[ifmm.P_FP64]}, BF16 {its[ifmm.P_BF16]}")
+
+
+def _far_majorant(h2, x):
+    """|U| |T| ... |U^T| |x|: the far field of the FMM product with every
+    operator and the vector replaced by their absolute values (the near field
+    left out), from the oracle's matvec."""
+    import copy
+    a = copy.copy(h2)
+    a.leafU = [np.abs(U) for U in h2.leafU]
+    a.transfer = [np.abs(T) for T in h2.transfer]
+    a.m2l = lambda l, i, q: np.abs(h2.m2l(l, i, q))
+    a.p2p = lambda i, j: np.zeros((len(h2.leaf_pts(i)), len(h2.leaf_pts(j))))
+    return a.matvec(np.abs(x))
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_fp32_far_field_matvec(ctx, name):
+    """fmm_matvec_prec: FP64 is fmm_matvec bit for bit; FP32 takes the far
+    field (P2M, M2M, M2L, L2L, L2P) in FP32 and the near field in FP64.
+    Bound, per element, against the oracle's FP64 product: the far field's
+    rounding is at most gamma_n |U||T|...|U^T||x| (the oracle's majorant) with
+    n the longest chain of accumulated terms (leaf size + (L-2) 8 n^D for M2M
+    + (L-1) 190 n^D for the M2L/L2L rows + n^D for L2P + one narrowing per
+    stage), gamma_n = n 2^-24 / (1 - n 2^-24); the near field and FP64 sums add
+    1e-13 of |y|.  Normwise the error must also stay below 1e-5 (the chains'
+    errors are not all aligned: typically ~1e-7) and above 1e-10 (so the far
+    field really ran in FP32)."""
+    from tests.gpu_util import oracle_h2, to_user
+    w = CASES[name]()
+    h2 = oracle_h2(w)
+    p = h2.tree.perm
+    X = w.rhs(3)
+    y_o = np.stack([to_user(h2, h2.matvec(X[p, c])) for c in range(3)], axis=1)
+    F = np.stack([to_user(h2, _far_majorant(h2, X[p, c])) for c in range(3)], axis=1)
+    sys = ifmm.ifmm_system_create(ctx, cuda(w.points), kernel(w), opts(w))
+    try:
+        xd = cuda(X.T.copy())
+        y64, yp64, y32 = (torch.empty_like(xd) for _ in range(3))
+        ifmm.fmm_matvec(ctx, sys, ifmm.MV_FMM, xd, y64, w.N)
+        ifmm.fmm_matvec_prec(ctx, sys, ifmm.P_FP64, xd, yp64, w.N)
+        ifmm.fmm_matvec_prec(ctx, sys, ifmm.P_FP32, xd, y32, w.N)
+        torch.cuda.synchronize()
+        assert torch.equal(y64, yp64)
+        got = y32.cpu().numpy().T
+        L, nd = h2.L, h2.nd
+        lv = h2.tree.levels[L]
+        mmax = int(np.max(lv.pt_end - lv.pt_begin))
+        n = mmax + (L - 2) * 8 * nd + (L - 1) * 190 * nd + nd + (L + 2)
+        gam = n * 2.0 ** -24 / (1 - n * 2.0 ** -24)
+        err = np.abs(got - y_o)
+        tol = gam * F + 1e-13 * np.abs(y_o) + 1e-300
+        nerr = np.linalg.norm(got - y_o) / np.linalg.norm(y_o)
+        print(f"{name}: FP32 far field, |y32 - y| / |y| = {nerr:.1e}, max err / bound "
+              f"{np.max(err / tol):.1e} (gamma_n {gam:.1e}, n {n})")
+        assert np.all(err <= tol)
+        assert 1e-10 < nerr < 1e-5
+    finally:
+        ifmm.ifmm_system_destroy(sys)
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_gmres_iterative_refinement(ctx, name):
+    """GMRES-IR (matvec_precision FP32): inner products with the FP32 far
+    field, FP64 true residuals.  With FP32 sweeps (flexible) and with FP64
+    sweeps (right) every column reaches the true residual 1e-10 and its
+    solution lies within kappa(A_n) x 2e-10 of the FP64 oracle's GMRES
+    solution (tol 1e-10).  Inner iteration counts are printed next to FP64
+    GMRES's.  IR with left preconditioning, the direct product or block GMRES
+    is refused."""
+    from oracle.gmres import gmres as oracle_gmres
+    from oracle.ifmm import IFMM
+    from tests.gpu_util import oracle_h2, to_user
+    w = CASES[name]()
+    h2 = oracle_h2(w)
+    kappa = np.linalg.cond(h2.dense_blockwise())
+    ora = IFMM(h2, w.eps)
+    p = h2.tree.perm
+    B = w.rhs(3)
+    X_o = np.stack([oracle_gmres(lambda v: to_user(h2, h2.matvec(v[p])), B[:, c], ora.solve,
+                                 1e-10, 500)[0] for c in range(3)], axis=1)
+    sys = ifmm.ifmm_system_create(ctx, cuda(w.points), kernel(w), opts(w, schur=ifmm.P_FP32))
+    try:
+        fac = ifmm.ifmm_factor(ctx, sys)
+        try:
+            Bd = cuda(B.T.copy())
+            x64 = torch.empty_like(Bd)
+            r64 = ifmm.gmres_solve(ctx, sys, fac, ifmm.MV_FMM, Bd, x64, w.N, 1e-10, 300)
+            out = {}
+            for label, side, pp in (("flexible/FP32 sweeps", ifmm.GMRES_FLEXIBLE, ifmm.P_FP32),
+                                    ("right/FP64 sweeps", ifmm.GMRES_RIGHT, ifmm.P_FP64)):
+                x = torch.empty_like(Bd)
+                reps = ifmm.gmres_solve_ex(ctx, sys, fac, ifmm.MV_FMM, Bd, x, w.N, 1e-10, 300,
+                                           side=side, refine=10, precond_precision=pp,
+                                           matvec_precision=ifmm.P_FP32)
+                assert all(r.status == 0 and r.true_rel_residual <= 1e-10 for r in reps), \
+                    [(r.iters, r.true_rel_residual) for r in reps]
+                e = rel(x.cpu().numpy().T, X_o)
+                assert e <= max(1e-12, 2e-10 * kappa), (label, e)
+                out[label] = ([r.iters for r in reps], e)
+            print(f"{name}: kappa {kappa:.1e}; FP64 GMRES iterations {[r.iters for r in r64]}; "
+                  + "; ".join(f"IR {k}: inner iterations {v[0]}, error vs oracle {v[1]:.1e}"
+                              for k, v in out.items()))
+            for kw in (dict(side=ifmm.GMRES_LEFT), dict(block=1)):
+                with pytest.raises(ifmm.IFMMError) as err:
+                    ifmm.gmres_solve_ex(ctx, sys, fac, ifmm.MV_FMM, Bd, torch.empty_like(Bd), w.N,
+                                        1e-10, 300, matvec_precision=ifmm.P_FP32, **kw)
+                assert err.value.status == 1
+            with pytest.raises(ifmm.IFMMError) as err:
+                ifmm.gmres_solve_ex(ctx, sys, fac, ifmm.MV_DIRECT, Bd, torch.empty_like(Bd), w.N,
+                                    1e-10, 300, matvec_precision=ifmm.P_FP32)
+            assert err.value.status == 1
+        finally:
+            ifmm.ifmm_factor_destroy(fac)
+    finally:
+        ifmm.ifmm_system_destroy(sys)

@@ -71,12 +71,18 @@ def test_factor_batch_matches_one_at_a_time(ctx, systems):
             ifmm.ifmm_factor_destroy(f)
 
 
-def test_server_results_same_alone_and_in_mix(ctx, systems):
+@pytest.mark.parametrize("mv", [ifmm.P_FP64, ifmm.P_FP32])
+def test_server_results_same_alone_and_in_mix(ctx, systems, mv):
+    """mv: the served GMRES's products in FP64, or iterative refinement with
+    the FP32 far field (set before registration; refused afterwards)."""
     ws, sys = systems
     facs = ifmm.ifmm_factor_batch(ctx, sys)
     srv = ifmm.ifmm_server_create(ctx, 64 << 30, workers=3)
     try:
+        ifmm.ifmm_server_set_matvec_precision(srv, mv)
         ids = [ifmm.ifmm_server_register(srv, s, f, maxit=100) for s, f in zip(sys, facs)]
+        with pytest.raises(ifmm.ServerError):
+            ifmm.ifmm_server_set_matvec_precision(srv, mv)
         rng = np.random.default_rng(77)
         reqs = []  # (system index, b)
         for k in range(14):
