@@ -10,13 +10,19 @@ and registered with the GMRES server under a 160 GB device-memory budget;
 systems that do not fit are refused.  Requests arrive as a Poisson process of
 2000 per second, each for a system drawn uniformly from the 64 and carrying
 1..32 standard-normal right-hand sides, solved by GMRES to a true residual of
-1e-10 (FP64 FMM products, orthogonalisation and residuals; FP32 substitution
-sweeps in flexible GMRES).  A step is `--step-seconds` of arrivals; the timed
+1e-10: GMRES with iterative refinement -- inner flexible GMRES whose FMM
+products take the far field in FP32 (near field FP64) and whose substitution
+sweeps run in FP32, outer FP64 FMM residuals (``--matvec fp64``: every product
+in FP64).  A step is `--step-seconds` of arrivals; the timed
 region is K consecutive steps, inputs resident on the device (requests carry
 device pointers).  ``value`` = right-hand sides solved to 1e-10 within the
 timed region per second; p50/p99 latency over the requests admitted in it;
 shed and refused counts.  ``e2e`` repeats a window with host-buffer requests
-(b copied in, x copied out by the server).  The factorisation of the
+(b copied in, x copied out by the server).  ``plain_fp64_one_at_a_time``
+solves a bounded sample of the same request stream one right-hand side at a
+time with plain FP64 GMRES (FP64 products and sweeps, no server, no batching)
+on the same resident factorisations -- the bar the served path is measured
+against.  The factorisation of the
 cube-64k system (N = 65,536, Chebyshev 4^3, eps = 1e-8) is timed in the
 mixed-precision symmetric form and in plain FP64 with the paper's general
 algorithm ("factor s vs plain FP64").
@@ -53,6 +59,7 @@ BUDGET = 160 * 10 ** 9     # device bytes admitted by the server
 RESIDENT_SHARE = 0.7       # of the budget for resident systems; the rest for GMRES blocks
 SERVE_CAP = 54             # rank cap 2 n^D of the serving systems (n = 3, D = 3)
 SERVE_MAXIT = 200
+RING_COLS = 96             # device output columns per system (see Load)
 
 
 def parse():
@@ -70,6 +77,9 @@ def parse():
     p.add_argument("--workers", type=int, default=8)
     p.add_argument("--schur", choices=["fp64", "fp32", "tf32"], default="fp32",
                    help="Schur-product precision of the timed path (fp32: split-TF32 tensor cores)")
+    p.add_argument("--matvec", choices=["fp32", "fp64"], default="fp32",
+                   help="served GMRES: fp32 = iterative refinement with the FMM far field in FP32 "
+                        "(FP64 residuals); fp64 = every product in FP64")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-plain", action="store_true",
@@ -313,6 +323,11 @@ class Load:
         self.ifmm, self.srv, self.ids, self.pools = ifmm, srv, ids, pools
         self.rng, self.device_inputs, self.torch, self.N = rng, device_inputs, torch, N
         self.pending = []
+        # device outputs: per system a ring of 96 columns, allocated before any
+        # timing.  At most 64 columns of a system are outstanding (one queued and
+        # one running block of <= 32), and a request never wraps (<= 31 columns
+        # skipped at the end), so live requests never share columns.
+        self.ring, self.head = {}, {}
         self.done = []          # (submit time, completion time, nrhs, worst residual, status)
         self.shed = 0
         self.refused = 0        # requests for systems the server did not admit
@@ -328,9 +343,13 @@ class Load:
         B = self.pools[i]
         try:
             if self.device_inputs:
-                x = self.torch.empty((k, self.N[i]), dtype=self.torch.float64, device=B.device)
+                h = self.head.get(i, 0)
+                if h + k > RING_COLS:
+                    h = 0
+                x = self.ring[i][h:h + k]
                 t = self.ifmm.ifmm_server_submit_device(self.srv, self.ids[i], B[:k], x, self.N[i],
                                                         1e-10, SERVE_MAXIT)
+                self.head[i] = h + k
             else:
                 import numpy as np
                 x = np.empty((k, self.N[i]))
@@ -384,6 +403,8 @@ def run_serving(args, ifmm, torch, ctx, dev, world, rank, dist):
                             rank_cap=SERVE_CAP)
     srv = ifmm.ifmm_server_create(ctx, BUDGET, workers=args.workers)
     ifmm.ifmm_server_set_reserve(srv, int((1.0 - RESIDENT_SHARE) * BUDGET))
+    ifmm.ifmm_server_set_matvec_precision(
+        srv, ifmm.P_FP32 if args.matvec == "fp32" else ifmm.P_FP64)
     try:
         return _serve(args, ifmm, torch, ctx, dev, world, rank, dist, ws, N, n_serve, opt, srv)
     finally:
@@ -444,6 +465,8 @@ def _serve(args, ifmm, torch, ctx, dev, world, rank, dist, ws, N, n_serve, opt, 
         pools_d[s] = torch.tensor(B, device=dev)
     rng = np.random.default_rng(5999 + rank)
     load = Load(ifmm, srv, ids, pools_d, rng, True, torch, N)
+    for s in admitted:
+        load.ring[s] = torch.empty((RING_COLS, N[s]), dtype=torch.float64, device=dev)
     for _ in range(args.warmup):           # plans of every block width, GPU clocks up
         load.run(args.step_seconds)
     load.drain()
@@ -486,22 +509,32 @@ def _serve(args, ifmm, torch, ctx, dev, world, rank, dist, ws, N, n_serve, opt, 
     # per-kernel profile (not timed: the event pairs cost time, and kernels of
     # concurrent workers would stretch each other's intervals): one 32-column
     # block of the largest admitted system, alone on one stream, through the
-    # same flexible GMRES with FP32 sweeps the server runs
+    # same GMRES the server runs
     big = max(admitted, key=lambda s_: N[s_])
     Bp = pools_d[big]
     Xp = torch.empty_like(Bp)
+    gopt = dict(side=ifmm.GMRES_FLEXIBLE, precond_precision=ifmm.P_FP32)
+    if args.matvec == "fp32":
+        gopt.update(matvec_precision=ifmm.P_FP32, refine=10)
     ifmm.gmres_solve_ex(ctx, systems[big], facs[big], ifmm.MV_FMM, Bp, Xp, N[big], 1e-10,
-                        SERVE_MAXIT, side=ifmm.GMRES_FLEXIBLE, precond_precision=ifmm.P_FP32)
+                        SERVE_MAXIT, **gopt)
     torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ifmm.gmres_solve_ex(ctx, systems[big], facs[big], ifmm.MV_FMM, Bp, Xp, N[big], 1e-10,
+                        SERVE_MAXIT, **gopt)
+    torch.cuda.synchronize()
+    block_s = time.perf_counter() - t0
     ifmm.ifmm_profile_start(ctx)
     t0 = time.perf_counter()
     preps = ifmm.gmres_solve_ex(ctx, systems[big], facs[big], ifmm.MV_FMM, Bp, Xp, N[big], 1e-10,
-                                SERVE_MAXIT, side=ifmm.GMRES_FLEXIBLE,
-                                precond_precision=ifmm.P_FP32)
+                                SERVE_MAXIT, **gopt)
     stats = ifmm.ifmm_profile_stop(ctx)
     prof_s = time.perf_counter() - t0
-    serve["profiled_block"] = {"system_N": N[big], "columns": 32, "seconds": prof_s,
+    serve["profiled_block"] = {"system_N": N[big], "columns": 32, "seconds": block_s,
+                               "seconds_under_launch_profile": prof_s,
                                "gmres_iterations_max": max(r.iters for r in preps)}
+    plain = None if args.no_plain else plain_one_at_a_time(ifmm, torch, ctx, systems, facs, ids,
+                                                           pools_d, N)
     # end to end: host-buffer requests through ifmm_server_submit
     e2e = None
     if not args.no_e2e:
@@ -516,8 +549,48 @@ def _serve(args, ifmm, torch, ctx, dev, world, rank, dist, ws, N, n_serve, opt, 
                "h2d_bytes_per_step": int(moved / n_e2e), "d2h_bytes_per_step": int(moved / n_e2e),
                "what": "the same request stream with b and x in host memory (ifmm_server_submit: "
                        "the server copies b in and x out inside each request's latency)"}
+    serve["plain_fp64_one_at_a_time"] = plain
     result = (value, lat, serve, factor_info, stats, prof_s, clk, e2e, launches, window)
     return result, (systems, facs)
+
+
+def plain_one_at_a_time(ifmm, torch, ctx, systems, facs, ids, pools, N, budget_s=20.0):
+    """The plain FP64 one-system-at-a-time path on the same request stream:
+    requests drawn as the load draws them (system uniform over the 64, 1-32
+    right-hand sides), each right-hand side solved alone by GMRES with FP64
+    products and FP64 sweeps (right preconditioning), no server and no
+    batching, on the resident factorisations; stops after budget_s seconds.
+    Requests for systems the server did not admit are skipped."""
+    import numpy as np
+    rng = np.random.default_rng(8000)
+    solved, worst, iters, reqs = 0, 0.0, [], 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        i = int(rng.integers(N_SYSTEMS))
+        k = int(rng.integers(1, 33))
+        if ids[i] is None:
+            continue
+        reqs += 1
+        for c in range(k):
+            b = pools[i][c]
+            x = torch.empty_like(b)
+            rep = ifmm.gmres_solve(ctx, systems[i], facs[i], ifmm.MV_FMM, b, x, N[i], 1e-10,
+                                   SERVE_MAXIT)[0]
+            if rep.status == 0:
+                solved += 1
+                worst = max(worst, rep.true_rel_residual)
+            iters.append(rep.iters)
+            if time.perf_counter() - t0 >= budget_s:
+                break
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    return {"value": solved / el, "unit": UNIT, "rhs_solved": solved, "requests": reqs,
+            "seconds": el, "worst_true_rel_residual": worst,
+            "gmres_iterations_p50": _pct(iters, 50) if iters else None,
+            "what": "each right-hand side alone through gmres_solve (FP64 FMM products, FP64 "
+                    "sweeps, right preconditioning), requests drawn like the served stream, on "
+                    "the same factorisations, until the time budget"}
 
 
 def factor_comparison(ifmm, torch, ctx, dev, schur):
@@ -601,8 +674,11 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * window / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64 GMRES (FMM products, CGS2, residuals) with f32 substitution sweeps; "
-                     "factors with split-TF32 Schur products (f32 accumulate), f64 LU/SVD",
+            "dtype": ("f64 GMRES residuals, CGS2 and outer products with iterative refinement: "
+                      "inner FMM far field f32 (near field f64), f32 substitution sweeps; "
+                      if args.matvec == "fp32" else
+                      "f64 GMRES (FMM products, CGS2, residuals) with f32 substitution sweeps; ")
+                     + "factors with split-TF32 Schur products (f32 accumulate), f64 LU/SVD",
             "data": "synthetic",
             "config": {"workload": serving_description() + (
                            "" if args.systems >= N_SYSTEMS else

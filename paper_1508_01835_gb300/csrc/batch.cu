@@ -431,6 +431,14 @@ ifmm_status ifmm_server_register(ifmm_server* s, ifmm_system* sys, ifmm_factoriz
     est += sizeof(float) * (size_t)n * n;
     bytes += est;
   }
+  if (s->precond_fp32) {  // the FP32 sweep plan for col_cap columns, if not built yet
+    size_t per_col = (size_t)sys->N;
+    for (int l = 2; l < (int)fac->yoff.size(); l++)
+      if (!fac->yoff[l].empty()) per_col += (size_t)fac->yoff[l].back();
+    for (const auto& R : fac->recs) per_col += (size_t)std::max(R.p, 1);
+    if (!fac->plans32.count(s->col_cap))  // one plan serves every width up to col_cap
+      bytes += sizeof(float) * per_col * s->col_cap + (size_t(8) << 20);
+  }
   {
     size_t fmm = ifmm::system_fmm_bytes(sys, s->col_cap);
     if (s->mv_fp32) fmm += ifmm::system_f32far_bytes(sys, s->col_cap);
@@ -450,7 +458,11 @@ ifmm_status ifmm_server_register(ifmm_server* s, ifmm_system* sys, ifmm_factoriz
     try {
       CK(cudaSetDevice(s->device));
       CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-      if (s->precond_fp32 && !fac->f32.ready) ifmm::factor_prepare_f32(fac, st);
+      if (s->precond_fp32) {
+        // the FP32 copies, and the sweep plan that serves every block width
+        ifmm::factor_prepare_f32(fac, st);
+        ifmm::factor_prepare_plans_f32(fac, s->col_cap, st);
+      }
       ifmm::system_prepare_fmm(sys, s->col_cap, st);
       if (s->mv_fp32) ifmm::system_prepare_f32far(sys, s->col_cap, st);
       CK(cudaStreamSynchronize(st));

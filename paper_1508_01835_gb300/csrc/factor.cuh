@@ -69,7 +69,7 @@ struct SolvePlan32 {
   std::vector<float*> w;
   std::vector<SpmmPlanF> steps;
   Arena task_mem;
-  GraphCache graph;
+  GraphSet graphs;  // per right-hand-side count (<= cap)
 };
 
 }  // namespace ifmm
@@ -93,6 +93,8 @@ struct ifmm_factorization {
   // specific to its column count, so alternating batch widths keep theirs)
   std::map<int, std::unique_ptr<ifmm::SolvePlan>> plans;
   ifmm::F32Data f32;
+  // FP32 plans by capacity: one plan of 32 columns serves every block of up
+  // to 32 right-hand sides (wider requests get a plan of their own width)
   std::map<int, std::unique_ptr<ifmm::SolvePlan32>> plans32;
   size_t plan_bytes() const {
     size_t b = f32.mem.held;
@@ -111,6 +113,8 @@ void factor_solve_f32(ifmm_factorization* f, const double* b, long long ldb, dou
                       long long ldx, int nrhs, cudaStream_t s);
 // Builds the FP32 copies (allocating); called by the first FP32 solve.
 void factor_prepare_f32(ifmm_factorization* f, cudaStream_t s);
+// Builds the FP32 substitution plan that serves up to max_cols columns now.
+void factor_prepare_plans_f32(ifmm_factorization* f, int max_cols, cudaStream_t s);
 struct GmresOpts {
   int side = IFMM_GMRES_RIGHT;  // ifmm_gmres_side
   int refine = 2;               // restarts from x when the true residual misses tol

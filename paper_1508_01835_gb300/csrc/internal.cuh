@@ -8,6 +8,7 @@
 #include <cstring>
 #include <functional>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <stdexcept>
 #include <string>
@@ -170,6 +171,17 @@ struct GraphCache {
 bool graphs_enabled();
 void run_graph(GraphCache& g, long long key, const char* name, cudaStream_t s,
                const std::function<void(cudaStream_t)>& body);
+// One graph per key (the right-hand-side count of a plan built for more
+// columns), so alternating block widths replay instead of re-capturing.
+struct GraphSet {
+  std::map<long long, std::unique_ptr<GraphCache>> g;
+  GraphCache& at(long long key) {
+    std::unique_ptr<GraphCache>& p = g[key];
+    if (!p) p.reset(new GraphCache());
+    return *p;
+  }
+  void reset() { g.clear(); }
+};
 
 // ---------------------------------------------------------------------------
 // Device memory: a chunked bump allocator.  Blocks are 256-byte aligned.
@@ -448,12 +460,13 @@ void validate_spmm(const std::vector<SpRow>& rows, const std::vector<SpEnt>& ent
 // results do not depend on scheduling.
 struct SpJob {
   int row, s0, ns;
-  long long part;  // offset of this job's partial sums; < 0: the job writes y
+  int r0, mt;      // rows r0 .. r0 + mt - 1 of the row (one tile of 8, 16 or 32 rows)
+  long long part;  // offset of this job's partial sums (mt rows); < 0: the job writes y
 };
 struct SpSeg { int ent, k0, k1; };
 struct SpRed {
-  int row, nj;
-  long long base;  // partial sums of job j of the row at base + j * m
+  int row, nj, r0, mt;
+  long long base;  // partial sums of job j of the tile at base + j * mt
 };
 struct SpmmPlan {
   const SpRow* rows = nullptr;
@@ -462,10 +475,13 @@ struct SpmmPlan {
   const SpSeg* segs = nullptr;
   const SpRed* reds = nullptr;
   int njobs = 0, nreds = 0;
+  int ncls[3] = {0, 0, 0};  // jobs per row class (m <= 8, <= 16, > 16), in that order
   double* part = nullptr;   // partial sums: part[job.part + r + c * part_ld]
   long long part_ld = 0;
   int cap = 0;              // right-hand sides per pass
-  double flops = 0.0, bytes = 0.0;  // per right-hand side
+  double flops = 0.0;   // per right-hand side
+  double bytes = 0.0;   // matrix entries, read once per pass of <= 32 right-hand sides
+  double vbytes = 0.0;  // x and y per right-hand side
 };
 // Plans rows/ents (uploaded to `ar`, with room for `cap` right-hand sides).
 SpmmPlan plan_spmm(Arena& ar, const std::vector<SpRow>& rows, const std::vector<SpEnt>& ents,
@@ -495,10 +511,13 @@ struct SpmmPlanF {
   const SpSeg* segs = nullptr;
   const SpRed* reds = nullptr;
   int njobs = 0, nreds = 0;
+  int ncls[3] = {0, 0, 0};  // jobs per row class (m <= 8, <= 16, > 16), in that order
   float* part = nullptr;
   long long part_ld = 0;
   int cap = 0;
-  double flops = 0.0, bytes = 0.0;  // flops per right-hand side; bytes per pass
+  double flops = 0.0;   // per right-hand side
+  double bytes = 0.0;   // matrix entries, read once per pass of <= 32 right-hand sides
+  double vbytes = 0.0;  // x and y per right-hand side
 };
 SpmmPlanF plan_spmm_f32(Arena& ar, const std::vector<SpRowF>& rows,
                         const std::vector<SpEntF>& ents, int cap, cudaStream_t s);

@@ -38,18 +38,21 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-__device__ __forceinline__ void load8(const float* p, float (&a)[8]) {
-  const float4 u = reinterpret_cast<const float4*>(p)[0];
-  const float4 v = reinterpret_cast<const float4*>(p)[1];
-  a[0] = u.x; a[1] = u.y; a[2] = u.z; a[3] = u.w;
-  a[4] = v.x; a[5] = v.y; a[6] = v.z; a[7] = v.w;
-}
-__device__ __forceinline__ void load8(const double* p, double (&a)[8]) {
+template <int N>
+__device__ __forceinline__ void load8_any(const float* p, float (&a)[N]) {
 #pragma unroll
-  for (int i = 0; i < 4; i++) {
-    const double2 v = reinterpret_cast<const double2*>(p)[i];
-    a[2 * i] = v.x;
-    a[2 * i + 1] = v.y;
+  for (int q = 0; q < N / 4; q++) {
+    const float4 u = reinterpret_cast<const float4*>(p)[q];
+    a[4 * q] = u.x; a[4 * q + 1] = u.y; a[4 * q + 2] = u.z; a[4 * q + 3] = u.w;
+  }
+}
+template <int N>
+__device__ __forceinline__ void load8_any(const double* p, double (&a)[N]) {
+#pragma unroll
+  for (int q = 0; q < N / 2; q++) {
+    const double2 v = reinterpret_cast<const double2*>(p)[q];
+    a[2 * q] = v.x;
+    a[2 * q + 1] = v.y;
   }
 }
 
@@ -58,31 +61,55 @@ __device__ __forceinline__ void load8(const double* p, double (&a)[8]) {
 constexpr int UNI_MAX_WARPS = 4;
 constexpr int UNI_NB = 32;
 
+// Lane tiling of an NDP x NBT output tile (NBT columns per pass): RGN row
+// groups of RPL rows times CGN column groups of CPL columns (columns j * CGN +
+// cg of lane cg); lanes beyond RGN * CGN idle (single-column passes of small
+// tables only).
+template <int NDP, int NBT>
+struct UniTile {
+  static constexpr int RPL = NBT == 32 ? 8 : NBT == 8 ? NDP / 8 : (NDP >= 32 ? NDP / 32 : 1);
+  static constexpr int RGN = NDP / RPL;
+  static constexpr int CGN = NBT == 32 ? 32 / RGN : NBT == 8 ? 4 : 1;
+  static constexpr int CPL = NBT / CGN;
+  static_assert(RGN * CGN <= 32 && CGN * CPL == NBT && RGN * RPL == NDP, "tile");
+};
+
 template <class T>
 __host__ __device__ constexpr int uni_xs(int ndp) {
   return ndp + 16 / (int)sizeof(T);  // column stride of the staged source block
 }
 template <class T>
-__host__ __device__ constexpr int uni_stage(int nd, int ndp) {
-  return nd * ndp + UNI_NB * uni_xs<T>(ndp);  // elements per stage
+__host__ __device__ constexpr int uni_stage(int nd, int ndp, int nbt) {
+  return nd * ndp + nbt * uni_xs<T>(ndp);  // elements per stage
 }
 
-template <class T, int RG>
+template <class T, int N>
+__device__ __forceinline__ void loadn(const T* p, T (&a)[N]) {
+  if constexpr (N * sizeof(T) % 16 == 0) {
+    load8_any(p, a);
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; i++) a[i] = p[i];
+  }
+}
+
+template <class T, int NDP, int NBT>
 __global__ void __launch_bounds__(32 * UNI_MAX_WARPS)
     k_uniform(const UniRow<T>* __restrict__ rows, const UniEnt<T>* __restrict__ ents, int nrows,
               int nd, int c0, int nb) {
-  constexpr int NDP = 8 * RG;
-  constexpr int CG = 32 / RG;
+  using Tl = UniTile<NDP, NBT>;
+  constexpr int RPL = Tl::RPL, RGN = Tl::RGN, CGN = Tl::CGN, CPL = Tl::CPL;
   constexpr int VN = 16 / (int)sizeof(T);
   constexpr int XS = uni_xs<T>(NDP);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row = blockIdx.x * (int)(blockDim.x >> 5) + warp;
   if (row >= nrows) return;  // warp-uniform; no block-wide barrier below
-  const int stage = uni_stage<T>(nd, NDP);
+  const int stage = uni_stage<T>(nd, NDP, NBT);
   T* buf = reinterpret_cast<T*>(smem_raw) + (size_t)warp * 2 * stage;
   const UniRow<T> R = rows[row];
-  const int rg = lane / CG, cg = lane % CG;
+  const int rg = lane / CGN, cg = lane % CGN;
+  const bool active = rg < RGN;
 
   auto prefetch = [&](int e, T* st) {
     const UniEnt<T> E = ents[R.e0 + e];
@@ -90,7 +117,7 @@ __global__ void __launch_bounds__(32 * UNI_MAX_WARPS)
     T* Xs = st + nd * NDP;
     const int achunks = nd * (NDP / VN);
     for (int q = lane; q < achunks; q += 32) cp_async16(As + q * VN, E.A + (size_t)q * VN, true);
-    const int xchunks = UNI_NB * (NDP / VN);
+    const int xchunks = NBT * (NDP / VN);
     for (int q = lane; q < xchunks; q += 32) {
       const int c = q / (NDP / VN), k4 = q % (NDP / VN);
       const bool ok = c < nb;
@@ -100,11 +127,11 @@ __global__ void __launch_bounds__(32 * UNI_MAX_WARPS)
     cp_async_commit();
   };
 
-  T acc[8][RG];
+  T acc[RPL][CPL];
 #pragma unroll
-  for (int i = 0; i < 8; i++)
+  for (int i = 0; i < RPL; i++)
 #pragma unroll
-    for (int j = 0; j < RG; j++) acc[i][j] = T(0);
+    for (int j = 0; j < CPL; j++) acc[i][j] = T(0);
 
   if (R.ne > 0) prefetch(0, buf);
   for (int e = 0; e < R.ne; e++) {
@@ -116,30 +143,33 @@ __global__ void __launch_bounds__(32 * UNI_MAX_WARPS)
       cp_async_wait<0>();
     }
     __syncwarp();
-    const T* As = cur + rg * 8;
-    const T* Xs = cur + nd * NDP + cg;
+    if (active) {
+      const T* As = cur + rg * RPL;
+      const T* Xs = cur + nd * NDP + cg * XS;
 #pragma unroll 3
-    for (int k = 0; k < nd; k++) {
-      T a[8];
-      load8(As + k * NDP, a);
-      T xv[RG];
+      for (int k = 0; k < nd; k++) {
+        T a[RPL];
+        loadn<T, RPL>(As + k * NDP, a);
+        T xv[CPL];
 #pragma unroll
-      for (int j = 0; j < RG; j++) xv[j] = Xs[(j * CG) * XS + k];
+        for (int j = 0; j < CPL; j++) xv[j] = Xs[(j * CGN) * XS + k];
 #pragma unroll
-      for (int i = 0; i < 8; i++)
+        for (int i = 0; i < RPL; i++)
 #pragma unroll
-        for (int j = 0; j < RG; j++) acc[i][j] = fma(a[i], xv[j], acc[i][j]);
+          for (int j = 0; j < CPL; j++) acc[i][j] = fma(a[i], xv[j], acc[i][j]);
+      }
     }
     __syncwarp();  // the stage is refilled by the next prefetch
   }
+  if (!active) return;
 #pragma unroll
-  for (int j = 0; j < RG; j++) {
-    const int c = j * CG + cg;
+  for (int j = 0; j < CPL; j++) {
+    const int c = j * CGN + cg;
     if (c >= nb) continue;
     T* y = R.y + (long long)(c0 + c) * R.ldy;
 #pragma unroll
-    for (int i = 0; i < 8; i++) {
-      const int r = rg * 8 + i;
+    for (int i = 0; i < RPL; i++) {
+      const int r = rg * RPL + i;
       if (r < nd) y[r] = acc[i][j];
     }
   }
@@ -185,21 +215,29 @@ UniPlan<T> plan_uniform(Arena& ar, const std::vector<UniRow<T>>& rows,
 
 // warps per CTA: as many (<= 4) as fit 200 KB of double-buffered stages
 template <class T>
-static int uni_warps(int nd, int ndp) {
-  const int per = 2 * uni_stage<T>(nd, ndp) * (int)sizeof(T);
+static int uni_warps(int nd, int ndp, int nbt) {
+  const int per = 2 * uni_stage<T>(nd, ndp, nbt) * (int)sizeof(T);
   return std::max(1, std::min(UNI_MAX_WARPS, (200 << 10) / per));
 }
 
-template <class T, int RG>
-static void launch_rg(const UniPlan<T>& p, int c0, int nb, cudaStream_t s) {
-  const int warps = uni_warps<T>(p.nd, p.ndp);
-  const int smem = warps * 2 * uni_stage<T>(p.nd, p.ndp) * (int)sizeof(T);
-  set_max_dynamic_smem((const void*)k_uniform<T, RG>, smem);
+template <class T, int NDP, int NBT>
+static void launch_tile(const UniPlan<T>& p, int c0, int nb, cudaStream_t s) {
+  const int warps = uni_warps<T>(p.nd, NDP, NBT);
+  const int smem = warps * 2 * uni_stage<T>(p.nd, NDP, NBT) * (int)sizeof(T);
+  set_max_dynamic_smem((const void*)k_uniform<T, NDP, NBT>, smem);
   const int grid = (p.nrows + warps - 1) / warps;
-  k_uniform<T, RG><<<grid, 32 * warps, smem, s>>>(p.rows, p.ents, p.nrows, p.nd, c0, nb);
+  k_uniform<T, NDP, NBT><<<grid, 32 * warps, smem, s>>>(p.rows, p.ents, p.nrows, p.nd, c0, nb);
   CK_LAUNCH("k_uniform");
 }
 
+template <class T, int NDP>
+static void launch_ndp(const UniPlan<T>& p, int c0, int nb, cudaStream_t s) {
+  if (nb <= 1) launch_tile<T, NDP, 1>(p, c0, nb, s);
+  else if (nb <= 8) launch_tile<T, NDP, 8>(p, c0, nb, s);
+  else launch_tile<T, NDP, 32>(p, c0, nb, s);
+}
+
+// passes of up to 32 columns; each pass with the narrowest tile (1, 8, 32)
 template <class T>
 void launch_uniform(const UniPlan<T>& p, int nrhs, cudaStream_t s) {
   if (p.nrows <= 0 || nrhs <= 0) return;
@@ -207,11 +245,11 @@ void launch_uniform(const UniPlan<T>& p, int nrhs, cudaStream_t s) {
   for (int c0 = 0; c0 < nrhs; c0 += UNI_NB) {
     const int nb = std::min(UNI_NB, nrhs - c0);
     Prof pr(name, p.flops * nb, p.bytes, s);
-    switch (p.ndp / 8) {
-      case 1: launch_rg<T, 1>(p, c0, nb, s); break;
-      case 2: launch_rg<T, 2>(p, c0, nb, s); break;
-      case 4: launch_rg<T, 4>(p, c0, nb, s); break;
-      default: launch_rg<T, 8>(p, c0, nb, s); break;
+    switch (p.ndp) {
+      case 8: launch_ndp<T, 8>(p, c0, nb, s); break;
+      case 16: launch_ndp<T, 16>(p, c0, nb, s); break;
+      case 32: launch_ndp<T, 32>(p, c0, nb, s); break;
+      default: launch_ndp<T, 64>(p, c0, nb, s); break;
     }
   }
 }

@@ -152,81 +152,237 @@ __global__ void __launch_bounds__(256) k_direct(KSpec ks, int dim, const double*
   if (i < N) y[(long long)col * ldy + i] = acc;
 }
 
-// Block-row sparse product, one CTA per job (SpJob): 32 rows at a time, the
-// 8 warps take interleaved columns of each non-transposed segment (coalesced
-// 256-byte column pieces of A, one FMA per element); transposed segments go a
-// row per warp with the lanes along the column.  Per-warp sums meet in shared
-// memory in a fixed order.
-constexpr int SPMM_WARPS = 8;
-
-__device__ inline double warp_sum_d(double v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
+// Block-row sparse product, one warp per job (SpJob), for FP64 and FP32.
+// A pass serves up to 32 right-hand sides from one read of the job's matrix
+// entries: the x values of 32 matrix columns at a time are staged in the
+// warp's shared memory ([k][column], row stride 32 + 16 / sizeof(T)); lane
+// (r, g) of a row tile of MR rows (MR = 8, 16 or 32 from the row's height)
+// keeps rows r of the MR columns g*MR .. g*MR+MR-1 in registers, reading its
+// A value once per k (transposed entries read along the stored row) and its
+// x values as 16-byte shared-memory loads.  Sums run over the job's segments
+// in order; split rows meet in k_spmm_reduce / k_spmm_f32_reduce in job order,
+// so results do not depend on scheduling.
+constexpr int SW_WARPS = 8, SW_NB = 32;
+// k values per staged chunk: 32 (FP32) or 16 (FP64), so that a warp's stage
+// (x: KC x (NBT + pad), A: KC x MR) stays near 8 KB
+template <class T>
+__host__ __device__ constexpr int sw_kc() {
+  return sizeof(T) == 4 ? 32 : 16;
 }
 
-__global__ void __launch_bounds__(256) k_spmm_job(const SpRow* __restrict__ rows,
-                                                  const SpEnt* __restrict__ ents,
-                                                  const SpJob* __restrict__ jobs,
-                                                  const SpSeg* __restrict__ segs,
-                                                  double* __restrict__ part, long long pld,
-                                                  int c0, int nb) {
-  const SpJob J = jobs[blockIdx.x];
-  const SpRow R = rows[J.row];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  __shared__ double sacc[SPMM_WARPS][33];
-  __shared__ double sacc_t[32];
-  for (int c = 0; c < nb; c++) {
-    for (int rt = 0; rt < R.m; rt += 32) {
-      const int r = rt + lane;
-      const bool rin = r < R.m;
-      if (threadIdx.x < 32) sacc_t[threadIdx.x] = 0.0;
-      __syncthreads();
-      double acc = 0.0;
-      for (int si = J.s0; si < J.s0 + J.ns; si++) {
-        const SpSeg G = segs[si];
-        const SpEnt E = ents[G.ent];
-        const double* x = E.x + (long long)(c0 + c) * E.ldx;
-        if (!E.A) {  // identity: rows k0..k1 of this entry
-          if (wid == 0 && rin && r >= G.k0 && r < G.k1) acc = fma(E.alpha, x[r], acc);
-        } else if (!E.transA) {
-          if (rin) {
-            const double* a = E.A + r;
-            double s0 = 0.0, s1 = 0.0;
-            int col = G.k0 + wid;
-            for (; col + SPMM_WARPS < G.k1; col += 2 * SPMM_WARPS) {
-              s0 = fma(a[(long long)col * E.lda], x[col], s0);
-              s1 = fma(a[(long long)(col + SPMM_WARPS) * E.lda], x[col + SPMM_WARPS], s1);
-            }
-            if (col < G.k1) s0 = fma(a[(long long)col * E.lda], x[col], s0);
-            acc = fma(E.alpha, s0 + s1, acc);
-          }
-        } else {  // op(A) = A^T with A (k x m): output row r is column r of A
-          const int rmax = min(32, R.m - rt);
-          for (int rl = wid; rl < rmax; rl += SPMM_WARPS) {  // warp-uniform
-            const double* a = E.A + (long long)(rt + rl) * E.lda;
-            double d = 0.0;
-            for (int col = G.k0 + lane; col < G.k1; col += 32) d = fma(a[col], x[col], d);
-            d = warp_sum_d(d);
-            if (lane == 0) sacc_t[rl] = fma(E.alpha, d, sacc_t[rl]);
-          }
-        }
-      }
-      sacc[wid][lane] = acc;
-      __syncthreads();
-      if (wid == 0 && rin) {
-        double v = sacc_t[lane];
+template <class T>
+struct SpT;
+template <>
+struct SpT<double> {
+  using Row = SpRow;
+  using Ent = SpEnt;
+  __device__ static bool trans(const SpEnt& e) { return e.transA != 0; }
+};
+template <>
+struct SpT<float> {
+  using Row = SpRowF;
+  using Ent = SpEntF;
+  __device__ static bool trans(const SpEntF&) { return false; }
+};
+// staged x row stride (elements) for passes of NBT columns
+template <class T, int NBT>
+__host__ __device__ constexpr int sw_xs() {
+  return NBT + 16 / (int)sizeof(T);
+}
+// elements of one warp's stage: x (KC rows of sw_xs) then A (KC x MR)
+template <class T, int MR, int NBT>
+__host__ __device__ constexpr int sw_stage() {
+  return sw_kc<T>() * (sw_xs<T, NBT>() + MR);
+}
+
+// asynchronous element copy global -> shared (cp.async); a false `ok` copies
+// no bytes and zero-fills the element
+template <class T>
+__device__ __forceinline__ void cp_async_elem(T* smem, const T* gmem, bool ok) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  if constexpr (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem),
+                 "r"(ok ? 4 : 0)
+                 : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem),
+                 "r"(ok ? 8 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_drain() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+// n consecutive values, with 16-byte loads where n * sizeof(T) allows
+template <class T, int N>
+__device__ __forceinline__ void vload(const T* p, T (&v)[N]) {
+  if constexpr (N * sizeof(T) % 16 == 0) {
+    constexpr int VN = 16 / (int)sizeof(T);
 #pragma unroll
-        for (int w = 0; w < SPMM_WARPS; w++) v += sacc[w][lane];
-        if (J.part < 0) {
-          double* y = R.y + (long long)(c0 + c) * R.ldy + r;
-          *y = (R.beta == 0.0) ? v : fma(R.beta, *y, v);
-        } else {
-          part[J.part + r + (long long)c * pld] = v;
+    for (int q = 0; q < N / VN; q++) {
+      if constexpr (sizeof(T) == 4) {
+        const float4 u = reinterpret_cast<const float4*>(p)[q];
+        v[4 * q] = u.x; v[4 * q + 1] = u.y; v[4 * q + 2] = u.z; v[4 * q + 3] = u.w;
+      } else {
+        const double2 u = reinterpret_cast<const double2*>(p)[q];
+        v[2 * q] = u.x; v[2 * q + 1] = u.y;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; i++) v[i] = p[i];
+  }
+}
+
+template <class T, int MR, int NBT>
+__device__ __forceinline__ void spmm_warp_job(const typename SpT<T>::Row& R,
+                                              const typename SpT<T>::Ent* __restrict__ ents,
+                                              const SpJob& J, const SpSeg* __restrict__ segs,
+                                              T* __restrict__ part, long long pld, int c0,
+                                              int nb, T* xs, int lane) {
+  constexpr int CPL = NBT * MR / 32;  // columns per lane: 32 / MR column groups
+  constexpr int XS = sw_xs<T, NBT>();
+  constexpr int KC = sw_kc<T>();
+  T* as = xs + KC * XS;  // staged A: as[k * MR + row of the tile]
+  const int rl = lane % MR, g = lane / MR;
+  {  // the job's tile: rows J.r0 .. J.r0 + J.mt - 1 (J.mt <= MR)
+    const int r = J.r0 + rl;
+    const bool rin = rl < J.mt;
+    T acc[CPL];
+#pragma unroll
+    for (int j = 0; j < CPL; j++) acc[j] = T(0);
+    for (int si = J.s0; si < J.s0 + J.ns; si++) {
+      const SpSeg S = segs[si];
+      const typename SpT<T>::Ent E = ents[S.ent];
+      const bool tr = SpT<T>::trans(E);
+      for (int kc0 = S.k0; kc0 < S.k1; kc0 += KC) {
+        const int kk = min(KC, S.k1 - kc0);
+        __syncwarp();  // the previous chunk has been read
+        // the chunk's x and A values are copied with cp.async, all in flight
+        // together (padding columns and rows zero-filled)
+        for (int e = lane; e < kk * NBT; e += 32) {
+          const int k = e % kk, c = e / kk;
+          const bool ok = c < nb;
+          cp_async_elem(xs + k * XS + c, E.x + kc0 + k + (ok ? (long long)(c0 + c) * E.ldx : 0),
+                        ok);
+        }
+        if (E.A) {
+          if (!tr) {  // lanes along the tile's rows (contiguous in a column)
+            for (int e = lane; e < kk * MR; e += 32) {
+              const int rr = e % MR, k = e / MR;
+              const bool ok = rr < J.mt;
+              cp_async_elem(as + k * MR + rr,
+                            E.A + (ok ? J.r0 + rr : 0) + (long long)(kc0 + k) * E.lda, ok);
+            }
+          } else {  // lanes along k (contiguous in a stored row)
+            for (int e = lane; e < kk * MR; e += 32) {
+              const int k = e % kk, rr = e / kk;
+              const bool ok = rr < J.mt;
+              cp_async_elem(as + k * MR + rr,
+                            E.A + (long long)(ok ? J.r0 + rr : 0) * E.lda + kc0 + k, ok);
+            }
+          }
+        }
+        cp_async_drain();
+        __syncwarp();
+        const T* xr = xs + g * CPL;
+        if (!E.A) {  // identity: output row r takes x[r] (rows k0 .. k1 of this entry)
+          if (rin && r >= kc0 && r < kc0 + kk) {
+            const T* xk = xr + (r - kc0) * XS;
+#pragma unroll
+            for (int j = 0; j < CPL; j++) acc[j] = fma(E.alpha, xk[j], acc[j]);
+          }
+        } else if (rin) {
+#pragma unroll 4
+          for (int k = 0; k < kk; k++) {
+            const T av = E.alpha * as[k * MR + rl];
+            T v[CPL];
+            vload<T, CPL>(xr + k * XS, v);
+#pragma unroll
+            for (int j = 0; j < CPL; j++) acc[j] = fma(av, v[j], acc[j]);
+          }
         }
       }
-      __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < CPL; j++) {
+      const int c = g * CPL + j;
+      if (!rin || c >= nb) continue;
+      if (J.part < 0) {
+        T* y = R.y + (long long)(c0 + c) * R.ldy + r;
+        *y = (R.beta == T(0)) ? acc[j] : fma(R.beta, *y, acc[j]);
+      } else {
+        part[J.part + rl + (long long)c * pld] = acc[j];
+      }
     }
   }
+}
+
+// jobs[0 .. njobs) all belong to rows of the class MR (m <= 8, <= 16, > 16);
+// passes of NBT (4 or 32) columns
+template <class T, int MR, int NBT>
+__global__ void __launch_bounds__(32 * SW_WARPS, 2)
+    k_spmm_warp(const typename SpT<T>::Row* __restrict__ rows,
+                const typename SpT<T>::Ent* __restrict__ ents, const SpJob* __restrict__ jobs,
+                int njobs, const SpSeg* __restrict__ segs, T* __restrict__ part, long long pld,
+                int c0, int nb) {
+  extern __shared__ __align__(16) unsigned char sw_smem[];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int jb = blockIdx.x * SW_WARPS + w;
+  if (jb >= njobs) return;  // warp-uniform; no block-wide barrier in this kernel
+  T* xs = reinterpret_cast<T*>(sw_smem) + (size_t)w * sw_stage<T, MR, NBT>();
+  const SpJob J = jobs[jb];
+  const typename SpT<T>::Row R = rows[J.row];
+  spmm_warp_job<T, MR, NBT>(R, ents, J, segs, part, pld, c0, nb, xs, lane);
+}
+
+// row class of a job: 0 (m <= 8), 1 (m <= 16), 2 (m > 16)
+static int sw_class(int m) { return m <= 8 ? 0 : m <= 16 ? 1 : 2; }
+
+template <class T, int MR, int NBT>
+static void launch_sw_tile(const typename SpT<T>::Row* rows, const typename SpT<T>::Ent* ents,
+                           const SpJob* jobs, int njobs, const SpSeg* segs, T* part,
+                           long long pld, int c0, int nb, cudaStream_t s) {
+  const int smem = SW_WARPS * sw_stage<T, MR, NBT>() * (int)sizeof(T);
+  set_max_dynamic_smem((const void*)k_spmm_warp<T, MR, NBT>, smem);
+  k_spmm_warp<T, MR, NBT><<<(njobs + SW_WARPS - 1) / SW_WARPS, 32 * SW_WARPS, smem, s>>>(
+      rows, ents, jobs, njobs, segs, part, pld, c0, nb);
+}
+template <class T, int MR>
+static void launch_sw_class(const typename SpT<T>::Row* rows, const typename SpT<T>::Ent* ents,
+                            const SpJob* jobs, int njobs, const SpSeg* segs, T* part,
+                            long long pld, int c0, int nb, cudaStream_t s) {
+  if (njobs <= 0) return;
+  if (nb <= 4) launch_sw_tile<T, MR, 4>(rows, ents, jobs, njobs, segs, part, pld, c0, nb, s);
+  else launch_sw_tile<T, MR, 32>(rows, ents, jobs, njobs, segs, part, pld, c0, nb, s);
+}
+
+// one launch per row class present (jobs grouped by class at plan time)
+template <class T>
+static void launch_spmm_warp(const typename SpT<T>::Row* rows, const typename SpT<T>::Ent* ents,
+                             const SpJob* jobs, const int* ncls, const SpSeg* segs, T* part,
+                             long long pld, int c0, int nb, cudaStream_t s) {
+  launch_sw_class<T, 8>(rows, ents, jobs, ncls[0], segs, part, pld, c0, nb, s);
+  launch_sw_class<T, 16>(rows, ents, jobs + ncls[0], ncls[1], segs, part, pld, c0, nb, s);
+  launch_sw_class<T, 32>(rows, ents, jobs + ncls[0] + ncls[1], ncls[2], segs, part, pld, c0, nb,
+                         s);
+}
+
+// jobs grouped by row class (stable); each job keeps its partial-sum slot
+template <class Row>
+static void group_jobs(const std::vector<Row>& rows, std::vector<SpJob>& jobs, int* ncls) {
+  std::vector<SpJob> out;
+  out.reserve(jobs.size());
+  for (int c = 0; c < 3; c++) {
+    ncls[c] = 0;
+    for (const SpJob& J : jobs)
+      if (sw_class(rows[J.row].m) == c) {
+        out.push_back(J);
+        ncls[c]++;
+      }
+  }
+  jobs.swap(out);
 }
 
 // y = beta y + (sum of the row's partial sums, in job order)
@@ -236,20 +392,22 @@ __global__ void __launch_bounds__(256) k_spmm_reduce(const SpRow* __restrict__ r
                                                      long long pld, int c0, int nb) {
   const SpRed D = reds[blockIdx.x];
   const SpRow R = rows[D.row];
-  // every thread takes (row, column) pairs: all threads busy for short rows
-  for (int e = threadIdx.x; e < R.m * nb; e += blockDim.x) {
-    const int r = e % R.m, c = e / R.m;
+  // every thread takes (row, column) pairs of the tile
+  for (int e = threadIdx.x; e < D.mt * nb; e += blockDim.x) {
+    const int r = e % D.mt, c = e / D.mt;
     const double* pp = part + D.base + r + (long long)c * pld;
     double v = 0.0;
-    for (int j = 0; j < D.nj; j++) v += pp[(long long)j * R.m];
-    double* y = R.y + (long long)(c0 + c) * R.ldy + r;
+    for (int j = 0; j < D.nj; j++) v += pp[(long long)j * D.mt];
+    double* y = R.y + (long long)(c0 + c) * R.ldy + D.r0 + r;
     *y = (R.beta == 0.0) ? v : fma(R.beta, *y, v);
   }
 }
 
-// Job split shared by the FP64 and FP32 products: about four jobs per SM, no
-// job below 8192 multiply-adds per right-hand side; a row whose work exceeds
-// the target is cut into up to 64 contiguous column ranges (partial sums).
+// Job split shared by the FP64 and FP32 products: every row is cut into tiles
+// of 8, 16 or 32 rows (the kernel's class for the row's height); a tile whose
+// work exceeds the target (about 32 jobs, one warp each, per SM; at least
+// 4096 multiply-adds per right-hand side) is cut into up to 64 contiguous
+// column ranges whose partial sums are added by the reduce kernel.
 template <class Row, class Ent>
 static void split_jobs(const std::vector<Row>& rows, const std::vector<Ent>& ents, int nsm,
                        std::vector<SpJob>& jobs, std::vector<SpSeg>& segs,
@@ -258,35 +416,38 @@ static void split_jobs(const std::vector<Row>& rows, const std::vector<Ent>& ent
   for (const Row& R : rows)
     for (int e = R.e0; e < R.e0 + R.ne; e++)
       total += (ents[e].A ? (double)R.m : 1.0) * ents[e].k;
-  const double target = std::max(8192.0, total / (4.0 * nsm));
+  const double target = std::max(4096.0, total / (32.0 * nsm));
   poff = 0;
   for (int ri = 0; ri < (int)rows.size(); ri++) {
     const Row& R = rows[ri];
     long long K = 0;
-    double work = 0.0;
-    for (int e = R.e0; e < R.e0 + R.ne; e++) {
-      K += ents[e].k;
-      work += (ents[e].A ? (double)R.m : 1.0) * ents[e].k;
-    }
-    int ns = (int)std::ceil(work / target);
-    if ((long long)ns > std::max(K, 1ll)) ns = (int)std::max(K, 1ll);
-    ns = std::max(1, std::min(ns, 64));
-    if (ns > 1) reds.push_back({ri, ns, poff});
-    for (int j = 0; j < ns; j++) {
-      const long long K0 = K * j / ns, K1 = K * (j + 1) / ns;
-      SpJob J{ri, (int)segs.size(), 0, ns > 1 ? poff + (long long)j * R.m : -1};
-      long long base = 0;
-      for (int e = R.e0; e < R.e0 + R.ne; e++) {
-        const long long lo = std::max(K0, base), hi = std::min(K1, base + ents[e].k);
-        if (lo < hi) {
-          segs.push_back({e, (int)(lo - base), (int)(hi - base)});
-          J.ns++;
+    for (int e = R.e0; e < R.e0 + R.ne; e++) K += ents[e].k;
+    const int mr = R.m <= 8 ? 8 : R.m <= 16 ? 16 : 32;  // rows per tile (the kernel's class)
+    for (int r0 = 0; r0 < R.m; r0 += mr) {
+      const int mt = std::min(mr, R.m - r0);
+      double work = 0.0;
+      for (int e = R.e0; e < R.e0 + R.ne; e++)
+        work += (ents[e].A ? (double)mt : 1.0) * ents[e].k;
+      int ns = (int)std::ceil(work / target);
+      if ((long long)ns > std::max(K, 1ll)) ns = (int)std::max(K, 1ll);
+      ns = std::max(1, std::min(ns, 64));
+      if (ns > 1) reds.push_back({ri, ns, r0, mt, poff});
+      for (int j = 0; j < ns; j++) {
+        const long long K0 = K * j / ns, K1 = K * (j + 1) / ns;
+        SpJob J{ri, (int)segs.size(), 0, r0, mt, ns > 1 ? poff + (long long)j * mt : -1};
+        long long base = 0;
+        for (int e = R.e0; e < R.e0 + R.ne; e++) {
+          const long long lo = std::max(K0, base), hi = std::min(K1, base + ents[e].k);
+          if (lo < hi) {
+            segs.push_back({e, (int)(lo - base), (int)(hi - base)});
+            J.ns++;
+          }
+          base += ents[e].k;
         }
-        base += ents[e].k;
+        jobs.push_back(J);
       }
-      jobs.push_back(J);
+      if (ns > 1) poff += (long long)ns * mt;
     }
-    if (ns > 1) poff += (long long)ns * R.m;
   }
 }
 
@@ -304,11 +465,12 @@ SpmmPlan plan_spmm(Arena& ar, const std::vector<SpRow>& rows, const std::vector<
   if (cap < 1) cap = 1;
   validate_spmm(rows, ents, cap);
   for (const SpRow& R : rows) {
-    P.bytes += 8.0 * R.m;
+    P.vbytes += 8.0 * R.m;
     for (int e = R.e0; e < R.e0 + R.ne; e++) {
       const SpEnt& E = ents[e];
       P.flops += 2.0 * R.m * (double)E.k;
-      P.bytes += 8.0 * E.k + (E.A ? 8.0 * R.m * (double)E.k : 0.0);
+      P.vbytes += 8.0 * E.k;
+      P.bytes += E.A ? 8.0 * R.m * (double)E.k : 0.0;
     }
   }
   std::vector<SpJob> jobs;
@@ -316,6 +478,7 @@ SpmmPlan plan_spmm(Arena& ar, const std::vector<SpRow>& rows, const std::vector<
   std::vector<SpRed> reds;
   long long poff = 0;
   split_jobs(rows, ents, sm_count(), jobs, segs, reds, poff);
+  group_jobs(rows, jobs, P.ncls);
   P.rows = upload(ar, rows, s);
   P.ents = upload(ar, ents, s);
   P.jobs = upload(ar, jobs, s);
@@ -330,99 +493,21 @@ SpmmPlan plan_spmm(Arena& ar, const std::vector<SpRow>& rows, const std::vector<
 }
 
 // ---------------------------------------------------------------------------
-// FP32 block-row products for the reduced-precision substitution sweeps: the
-// same job split, but every job serves all of its right-hand sides (up to 32
-// per pass) from one read of its matrix entries.  The x columns of a chunk of
-// 32 matrix columns are staged in shared memory; each warp walks a strided
-// subset of the chunk's columns for 32 output rows and keeps NB partial sums
-// per row in registers; the eight warps' sums are added through shared memory.
+// FP32 block-row products (reduced-precision sweeps, FP32 far field): the
+// same job split and the same warp kernel in FP32.
 // ---------------------------------------------------------------------------
-constexpr int F32_KCH = 32;
-
-template <int NB>
-__global__ void __launch_bounds__(256) k_spmm_f32(const SpRowF* __restrict__ rows,
-                                                  const SpEntF* __restrict__ ents,
-                                                  const SpJob* __restrict__ jobs,
-                                                  const SpSeg* __restrict__ segs,
-                                                  float* __restrict__ part, long long pld,
-                                                  int c0, int nb) {
-  const SpJob J = jobs[blockIdx.x];
-  const SpRowF R = rows[J.row];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  __shared__ __align__(16) float xs[F32_KCH][NB + 4];
-  __shared__ float red[SPMM_WARPS][32][NB + 1];
-  for (int rt = 0; rt < R.m; rt += 32) {
-    const int r = rt + lane;
-    const bool rin = r < R.m;
-    float acc[NB];
-#pragma unroll
-    for (int c = 0; c < NB; c++) acc[c] = 0.0f;
-    for (int si = J.s0; si < J.s0 + J.ns; si++) {
-      const SpSeg G = segs[si];
-      const SpEntF E = ents[G.ent];
-      for (int kc0 = G.k0; kc0 < G.k1; kc0 += F32_KCH) {
-        const int kk = min(F32_KCH, G.k1 - kc0);
-        __syncthreads();  // the previous chunk has been read
-        for (int e = threadIdx.x; e < kk * NB; e += blockDim.x) {
-          const int col = e % kk, c = e / kk;
-          xs[col][c] = c < nb ? E.x[kc0 + col + (long long)(c0 + c) * E.ldx] : 0.0f;
-        }
-        __syncthreads();
-        if (!E.A) {  // identity: output row r takes x[r] (rows kc0 .. kc0 + kk)
-          if (wid == 0 && rin && r >= kc0 && r < kc0 + kk) {
-#pragma unroll
-            for (int c = 0; c < NB; c++) acc[c] = fmaf(E.alpha, xs[r - kc0][c], acc[c]);
-          }
-        } else if (rin) {
-          const float* a = E.A + r + (long long)kc0 * E.lda;
-          for (int col = wid; col < kk; col += SPMM_WARPS) {
-            const float av = E.alpha * a[(long long)col * E.lda];
-            const float4* xv = reinterpret_cast<const float4*>(&xs[col][0]);
-#pragma unroll
-            for (int q = 0; q < NB / 4; q++) {
-              const float4 v = xv[q];
-              acc[4 * q + 0] = fmaf(av, v.x, acc[4 * q + 0]);
-              acc[4 * q + 1] = fmaf(av, v.y, acc[4 * q + 1]);
-              acc[4 * q + 2] = fmaf(av, v.z, acc[4 * q + 2]);
-              acc[4 * q + 3] = fmaf(av, v.w, acc[4 * q + 3]);
-            }
-          }
-        }
-      }
-    }
-#pragma unroll
-    for (int c = 0; c < NB; c++) red[wid][lane][c] = acc[c];
-    __syncthreads();
-    for (int e = threadIdx.x; e < 32 * nb; e += blockDim.x) {
-      const int rl = e % 32, c = e / 32, row = rt + rl;
-      if (row < R.m) {
-        float v = 0.0f;
-#pragma unroll
-        for (int w = 0; w < SPMM_WARPS; w++) v += red[w][rl][c];
-        if (J.part < 0) {
-          float* y = R.y + (long long)(c0 + c) * R.ldy + row;
-          *y = (R.beta == 0.0f) ? v : fmaf(R.beta, *y, v);
-        } else {
-          part[J.part + row + (long long)c * pld] = v;
-        }
-      }
-    }
-    __syncthreads();
-  }
-}
-
 __global__ void __launch_bounds__(256) k_spmm_f32_reduce(const SpRowF* __restrict__ rows,
                                                          const SpRed* __restrict__ reds,
                                                          const float* __restrict__ part,
                                                          long long pld, int c0, int nb) {
   const SpRed D = reds[blockIdx.x];
   const SpRowF R = rows[D.row];
-  for (int e = threadIdx.x; e < R.m * nb; e += blockDim.x) {
-    const int r = e % R.m, c = e / R.m;
+  for (int e = threadIdx.x; e < D.mt * nb; e += blockDim.x) {
+    const int r = e % D.mt, c = e / D.mt;
     const float* pp = part + D.base + r + (long long)c * pld;
     float v = 0.0f;
-    for (int j = 0; j < D.nj; j++) v += pp[(long long)j * R.m];
-    float* y = R.y + (long long)(c0 + c) * R.ldy + r;
+    for (int j = 0; j < D.nj; j++) v += pp[(long long)j * D.mt];
+    float* y = R.y + (long long)(c0 + c) * R.ldy + D.r0 + r;
     *y = (R.beta == 0.0f) ? v : fmaf(R.beta, *y, v);
   }
 }
@@ -434,13 +519,14 @@ SpmmPlanF plan_spmm_f32(Arena& ar, const std::vector<SpRowF>& rows,
   if (cap < 1) cap = 1;
   for (const SpRowF& R : rows) {
     Ranges::check(R.y, sizeof(float) * ((size_t)(cap - 1) * R.ldy + R.m), "spmm32 y");
-    P.bytes += 4.0 * R.m;
+    P.vbytes += 4.0 * R.m;
     for (int e = R.e0; e < R.e0 + R.ne; e++) {
       const SpEntF& E = ents[e];
       if (E.A) Ranges::check(E.A, sizeof(float) * ((size_t)(E.k - 1) * E.lda + R.m), "spmm32 A");
       Ranges::check(E.x, sizeof(float) * ((size_t)(cap - 1) * E.ldx + E.k), "spmm32 x");
       P.flops += 2.0 * R.m * (double)E.k;
-      P.bytes += 4.0 * E.k + (E.A ? 4.0 * R.m * (double)E.k : 0.0);
+      P.vbytes += 4.0 * E.k;
+      P.bytes += E.A ? 4.0 * R.m * (double)E.k : 0.0;
     }
   }
   std::vector<SpJob> jobs;
@@ -448,6 +534,7 @@ SpmmPlanF plan_spmm_f32(Arena& ar, const std::vector<SpRowF>& rows,
   std::vector<SpRed> reds;
   long long poff = 0;
   split_jobs(rows, ents, sm_count(), jobs, segs, reds, poff);
+  group_jobs(rows, jobs, P.ncls);
   P.rows = upload(ar, rows, s);
   P.ents = upload(ar, ents, s);
   P.jobs = upload(ar, jobs, s);
@@ -463,18 +550,12 @@ SpmmPlanF plan_spmm_f32(Arena& ar, const std::vector<SpRowF>& rows,
 
 void launch_spmm_f32(const SpmmPlanF& p, int nrhs, cudaStream_t s) {
   if (p.njobs <= 0 || nrhs <= 0) return;
-  for (int c0 = 0; c0 < nrhs; c0 += 32) {
-    const int nb = std::min(32, nrhs - c0);
+  for (int c0 = 0; c0 < nrhs; c0 += SW_NB) {
+    const int nb = std::min(SW_NB, nrhs - c0);
     {
-      Prof pr("k_spmm_f32", p.flops * nb, p.bytes, s);
-      if (nb <= 4)
-        k_spmm_f32<4><<<p.njobs, 256, 0, s>>>(p.rows, p.ents, p.jobs, p.segs, p.part, p.part_ld, c0, nb);
-      else if (nb <= 8)
-        k_spmm_f32<8><<<p.njobs, 256, 0, s>>>(p.rows, p.ents, p.jobs, p.segs, p.part, p.part_ld, c0, nb);
-      else if (nb <= 16)
-        k_spmm_f32<16><<<p.njobs, 256, 0, s>>>(p.rows, p.ents, p.jobs, p.segs, p.part, p.part_ld, c0, nb);
-      else
-        k_spmm_f32<32><<<p.njobs, 256, 0, s>>>(p.rows, p.ents, p.jobs, p.segs, p.part, p.part_ld, c0, nb);
+      Prof pr("k_spmm_f32", p.flops * nb, p.bytes + p.vbytes * nb, s);
+      launch_spmm_warp<float>(p.rows, p.ents, p.jobs, p.ncls, p.segs, p.part, p.part_ld, c0, nb,
+                              s);
       CK_LAUNCH("k_spmm_f32");
     }
     if (p.nreds > 0) {
@@ -603,12 +684,13 @@ void launch_scatter_rows_add(const long long* perm, long long N, const double* i
 
 void launch_spmm(const SpmmPlan& p, int nrhs, cudaStream_t s) {
   if (p.njobs <= 0 || nrhs <= 0) return;
-  for (int c0 = 0; c0 < nrhs; c0 += p.cap) {
-    const int nb = std::min(p.cap, nrhs - c0);
+  const int step = std::min(p.cap, SW_NB);  // the partial sums hold cap columns
+  for (int c0 = 0; c0 < nrhs; c0 += step) {
+    const int nb = std::min(step, nrhs - c0);
     {
-      Prof pr("k_spmm_job", p.flops * nb, p.bytes * nb, s);
-      k_spmm_job<<<p.njobs, 256, 0, s>>>(p.rows, p.ents, p.jobs, p.segs, p.part, p.part_ld, c0,
-                                         nb);
+      Prof pr("k_spmm_job", p.flops * nb, p.bytes + p.vbytes * nb, s);
+      launch_spmm_warp<double>(p.rows, p.ents, p.jobs, p.ncls, p.segs, p.part, p.part_ld, c0, nb,
+                               s);
       CK_LAUNCH("k_spmm_job");
     }
     if (p.nreds > 0) {

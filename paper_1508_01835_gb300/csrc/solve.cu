@@ -200,7 +200,7 @@ void factor_prepare_f32(ifmm_factorization* f, cudaStream_t s) {
 }
 
 static void build_plan32(ifmm_factorization* f, SolvePlan32& P, int nrhs, cudaStream_t s) {
-  P.graph.reset();
+  P.graphs.reset();
   P.steps.clear();
   P.mem.release();
   P.task_mem.release();
@@ -305,22 +305,33 @@ static void build_plan32(ifmm_factorization* f, SolvePlan32& P, int nrhs, cudaSt
   CK(cudaStreamSynchronize(s));
 }
 
+constexpr int PLAN32_COLS = 32;
+
+static SolvePlan32& plan32_for(ifmm_factorization* f, int nrhs, cudaStream_t s) {
+  const int cap = std::max(nrhs, PLAN32_COLS);
+  std::unique_ptr<SolvePlan32>& slot = f->plans32[cap];
+  if (!slot) {
+    CK(cudaStreamSynchronize(s));
+    factor_prepare_f32(f, s);
+    auto P = std::make_unique<SolvePlan32>();
+    build_plan32(f, *P, cap, s);
+    slot = std::move(P);
+  }
+  return *slot;
+}
+
+void factor_prepare_plans_f32(ifmm_factorization* f, int max_cols, cudaStream_t s) {
+  plan32_for(f, max_cols, s);
+}
+
 void factor_solve_f32(ifmm_factorization* f, const double* b, long long ldb, double* x,
                       long long ldx, int nrhs, cudaStream_t s) {
   if (nrhs <= 0) return;
   ifmm_system* sys = f->sys;
   const long long N = sys->N;
-  std::unique_ptr<SolvePlan32>& slot = f->plans32[nrhs];
-  if (!slot) {
-    CK(cudaStreamSynchronize(s));
-    factor_prepare_f32(f, s);
-    auto P = std::make_unique<SolvePlan32>();
-    build_plan32(f, *P, nrhs, s);
-    slot = std::move(P);
-  }
-  SolvePlan32& P = *slot;
+  SolvePlan32& P = plan32_for(f, nrhs, s);
   launch_gather_rows_f32(sys->perm, N, b, ldb, P.xt, N, nrhs, s);
-  run_graph(P.graph, nrhs, "graph:ifmm_solve_f32", s, [&](cudaStream_t gs) {
+  run_graph(P.graphs.at(nrhs), nrhs, "graph:ifmm_solve_f32", s, [&](cudaStream_t gs) {
     for (int l = 2; l <= sys->L; l++)
       CK(cudaMemsetAsync(P.ybar[l], 0, sizeof(float) * std::max(P.nybar[l], 1ll) * nrhs, gs));
     for (const SpmmPlanF& st : P.steps) launch_spmm_f32(st, nrhs, gs);

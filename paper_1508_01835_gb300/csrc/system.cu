@@ -240,7 +240,7 @@ static void make_padded_tables(ifmm_system* sys, ChebOps& ops, cudaStream_t s) {
 }
 
 static void build_fmm_plan(ifmm_system* sys, int cap, cudaStream_t s) {
-  sys->fmm_graph.reset();
+  sys->fmm_graphs.reset();
   sys->fmm_plan.phases.clear();
   sys->fmm_plan.mem.reset();
   sys->fmm_uni.clear();
@@ -384,7 +384,7 @@ void system_matvec(ifmm_system* sys, int mode, const double* x, long long ldx, d
     build_fmm_plan(sys, std::max(nrhs, 4), s);
   }
   launch_gather_rows(sys->perm, sys->N, x, ldx, sys->fmm_x, sys->N, nrhs, s);
-  run_graph(sys->fmm_graph, nrhs, "graph:fmm_matvec", s,
+  run_graph(sys->fmm_graphs.at(nrhs), nrhs, "graph:fmm_matvec", s,
             [&](cudaStream_t gs) { run_fmm_phases(sys, nrhs, gs); });
   launch_scatter_rows(sys->perm, sys->N, sys->fmm_y, sys->N, y, ldy, nrhs, s);
 }
@@ -453,7 +453,7 @@ static F32Sizes f32_sizes(const ifmm_system* sys, int cap) {
 static void build_f32_plan(ifmm_system* sys, int cap, cudaStream_t s) {
   build_f32_ops(sys, s);
   Fmm32& f = sys->f32;
-  f.graph.reset();
+  f.graphs.reset();
   f.far.clear();
   f.far_uni.clear();
   f.order.clear();
@@ -610,7 +610,7 @@ void system_matvec_f32far(ifmm_system* sys, const double* x, long long ldx, doub
     build_f32_plan(sys, std::max(nrhs, 4), s);
   }
   launch_gather_rows_2(sys->perm, sys->N, x, ldx, f.x64, f.x32, sys->N, nrhs, s);
-  run_graph(f.graph, nrhs, "graph:fmm_matvec_f32far", s, [&](cudaStream_t gs) {
+  run_graph(f.graphs.at(nrhs), nrhs, "graph:fmm_matvec_f32far", s, [&](cudaStream_t gs) {
     size_t a = 0, u = 0;
     for (int kind : f.order) {
       if (kind == 0) launch_spmm_f32(f.far[a++], nrhs, gs);

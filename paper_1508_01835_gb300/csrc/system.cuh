@@ -113,7 +113,7 @@ struct Fmm32 {
   double *x64 = nullptr, *y64 = nullptr;  // tree order
   float *x32 = nullptr, *y32 = nullptr;
   int cap = 0;
-  GraphCache graph;
+  GraphSet graphs;  // per right-hand-side count (<= cap)
 };
 
 struct SpBuild {
@@ -162,7 +162,7 @@ struct ifmm_system {
   ifmm::SpPlan fmm_plan;
   std::vector<ifmm::UniPlan<double>> fmm_uni;  // M2M, M2L + L2L phases (nd <= 64)
   std::vector<int> fmm_order;                  // 0: next fmm_plan phase, 1: next fmm_uni
-  ifmm::GraphCache fmm_graph;  // fmm_plan.run as one graph
+  ifmm::GraphSet fmm_graphs;   // the FMM phases as one graph per right-hand-side count
   int fmm_cap = 0;
   double *fmm_x = nullptr, *fmm_y = nullptr;
   ifmm::Fmm32 f32;                           // FP32 far field (made on first use)
