@@ -65,7 +65,10 @@ RING_COLS = 96             # device output columns per system (see Load)
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--steps", type=int, default=60,
+                   help="timed steps of --step-seconds of arrivals (default 30 s: longer than "
+                        "the largest systems' blocks, so the count does not hinge on which "
+                        "blocks happen to finish inside the window)")
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", choices=["serving-cube", "cube-64k", "cube-2k"],

@@ -7,6 +7,8 @@
         [--rate 200] [--seconds 10]
     python -m paper_1508_01835_gb300.run_case --mode paper [--d 1e-3] [--orders 1,2,3,4]
         [--fmm-n 5] [--leaf 100] [--N 100000]
+    python -m paper_1508_01835_gb300.run_case --mode blocks [--serving-systems 24,12]
+    python -m paper_1508_01835_gb300.run_case --mode kernels [--serving-systems 12]
 
 Each repetition: system creation (tree, lists, operators), factorisation
 (sigma_0, weighted bases, elimination, top LU) and FMM-GMRES to 1e-10 on one
@@ -25,6 +27,14 @@ second for --seconds; prints p50/p99 latency, solves/s and the shed count.
 Chebyshev order, eps, seed) at a smaller size, which is how the profiles
 capture a small case of the same kernels.  IFMM_TRACE=1 adds per-level and
 per-colour lines on stderr.
+``--mode blocks``: serving-cube systems as the server holds them (rank cap 54,
+split-TF32 Schur products, symmetric variant); per system the times of a
+32-column FMM product in FP64 and with the FP32 far field, of a 32-column
+substitution sweep in FP64 and FP32, and of GMRES to 1e-10 on 1 and 32
+right-hand sides with FP64 products (flexible, FP32 sweeps) and with
+iterative refinement (second of two runs each).  ``--mode kernels``: the
+same system set-up, then one FP32 far-field product and one FP32 sweep of 32
+columns, twice (a small target for ncu).
 """
 from __future__ import annotations
 
@@ -46,7 +56,10 @@ def main(argv=None):
     p.add_argument("--symmetric", action="store_true")
     p.add_argument("--reps", type=int, default=2)
     p.add_argument("--no-gmres", action="store_true")
-    p.add_argument("--mode", choices=["case", "batch", "serve", "paper"], default="case")
+    p.add_argument("--mode", choices=["case", "batch", "serve", "paper", "blocks", "kernels"],
+                   default="case")
+    p.add_argument("--serving-systems", default="24,12",
+                   help="--mode blocks / kernels: indices of serving-cube systems")
     p.add_argument("--d", type=float, default=1e-3)
     p.add_argument("--orders", default="1,2,3,4")
     p.add_argument("--fmm-n", type=int, default=5)
@@ -66,6 +79,8 @@ def main(argv=None):
         return serve(a)
     if a.mode == "paper":
         return paper(a)
+    if a.mode in ("blocks", "kernels"):
+        return blocks(a)
 
     import torch
 
@@ -109,6 +124,67 @@ def main(argv=None):
               f"top {info.seconds_top:.3f} bytes {info.factor_bytes / 1e9:.2f}GB", flush=True)
         ifmm.ifmm_factor_destroy(f)
         ifmm.ifmm_system_destroy(s)
+    ifmm.ifmm_ctx_destroy(ctx)
+
+
+def blocks(a):
+    """Per-block costs on serving-cube systems (see the module docstring)."""
+    import numpy as np
+    import torch
+
+    import paper_1508_01835_gb300 as ifmm
+    import workloads
+
+    ctx = ifmm.ifmm_ctx_create(0)
+
+    def timed(fn, reps=1):
+        fn()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(reps):
+            out = fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t) / reps, out
+
+    for si in [int(v) for v in a.serving_systems.split(",")]:
+        w = workloads.serving_cube_system(si)
+        opt = ifmm.make_options(dim=3, cheb_n=w.cheb_n, leaf_max=w.leaf_max, eps=w.eps,
+                                schur=ifmm.P_FP32, symmetric=1, rank_cap=54)
+        kern = ifmm.Kernel(w.kernel.kind, w.kernel.param, w.kernel.diag)
+        t0 = time.perf_counter()
+        sy = ifmm.ifmm_system_create(ctx, torch.tensor(w.points, device="cuda"), kern, opt)
+        fac = ifmm.ifmm_factor(ctx, sy, allow_singular=True)
+        torch.cuda.synchronize()
+        print(f"[serving-cube[{si}] N={w.N}] create+factor {time.perf_counter() - t0:.2f}s",
+              flush=True)
+        X = torch.tensor(np.random.default_rng(4).standard_normal((32, w.N)), device="cuda")
+        Y = torch.empty_like(X)
+        if a.mode == "kernels":
+            for _ in range(2):
+                ifmm.fmm_matvec_prec(ctx, sy, ifmm.P_FP32, X, Y, w.N)
+                ifmm.ifmm_solve_prec(ctx, fac, ifmm.P_FP32, X, Y, w.N)
+            torch.cuda.synchronize()
+        else:
+            for name, prec in (("fp64", ifmm.P_FP64), ("fp32-far", ifmm.P_FP32)):
+                dt, _ = timed(lambda: ifmm.fmm_matvec_prec(ctx, sy, prec, X, Y, w.N), 3)
+                print(f"  matvec 32 columns {name}: {dt * 1e3:.2f} ms", flush=True)
+            for name, prec in (("fp64", ifmm.P_FP64), ("fp32", ifmm.P_FP32)):
+                dt, _ = timed(lambda: ifmm.ifmm_solve_prec(ctx, fac, prec, X, Y, w.N), 3)
+                print(f"  sweep 32 columns {name}: {dt * 1e3:.2f} ms", flush=True)
+            for width in (1, 32):
+                B = X[:width].contiguous()
+                Z = torch.empty_like(B)
+                for name, kw in (("fp64 products", {}),
+                                 ("iterative refinement", dict(matvec_precision=ifmm.P_FP32,
+                                                               refine=10))):
+                    dt, reps = timed(lambda: ifmm.gmres_solve_ex(
+                        ctx, sy, fac, ifmm.MV_FMM, B, Z, w.N, 1e-10, 300,
+                        side=ifmm.GMRES_FLEXIBLE, precond_precision=ifmm.P_FP32, **kw))
+                    print(f"  GMRES {width} columns, {name}: {dt * 1e3:.1f} ms, iterations max "
+                          f"{max(r.iters for r in reps)}, true residual max "
+                          f"{max(r.true_rel_residual for r in reps):.2e}", flush=True)
+        ifmm.ifmm_factor_destroy(fac)
+        ifmm.ifmm_system_destroy(sy)
     ifmm.ifmm_ctx_destroy(ctx)
 
 
