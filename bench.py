@@ -597,8 +597,9 @@ def plain_one_at_a_time(ifmm, torch, ctx, systems, facs, ids, pools, N, budget_s
 
 
 def factor_comparison(ifmm, torch, ctx, dev, schur):
-    """cube-64k: factor time of the mixed-precision symmetric path vs plain FP64
-    with the paper's general algorithm, plus GMRES on each."""
+    """cube-64k: factor time of the mixed-precision symmetric path, of the same
+    symmetric variant in FP64 (precision alone) and of plain FP64 with the
+    paper's general algorithm, plus GMRES on each."""
     import numpy as np
 
     import workloads
@@ -607,8 +608,12 @@ def factor_comparison(ifmm, torch, ctx, dev, schur):
     pts = torch.tensor(w.points, device=dev)
     b = torch.tensor(w.rhs(1)[:, 0], device=dev)
     out = {}
+    # three legs: the timed path, the same algorithm in FP64 (the precision
+    # axis alone) and the paper's general algorithm in FP64 (the plain path)
     for name, o in (("mixed_symmetric", ifmm.make_options(dim=3, cheb_n=4, leaf_max=64, eps=w.eps,
                                                           schur=schur, symmetric=1)),
+                    ("fp64_symmetric", ifmm.make_options(dim=3, cheb_n=4, leaf_max=64, eps=w.eps,
+                                                         schur=ifmm.P_FP64, symmetric=1)),
                     ("plain_fp64_general", ifmm.make_options(dim=3, cheb_n=4, leaf_max=64,
                                                              eps=w.eps, schur=ifmm.P_FP64))):
         s = ifmm.ifmm_system_create(ctx, pts, kern, o)
@@ -626,8 +631,11 @@ def factor_comparison(ifmm, torch, ctx, dev, schur):
         out[name + "_x"] = x.cpu().numpy()
         ifmm.ifmm_factor_destroy(f)
         ifmm.ifmm_system_destroy(s)
-    xa, xb = out.pop("mixed_symmetric_x"), out.pop("plain_fp64_general_x")
+    xa, xs, xb = (out.pop(k + "_x") for k in ("mixed_symmetric", "fp64_symmetric",
+                                               "plain_fp64_general"))
     out["solution_difference"] = float(np.linalg.norm(xa - xb) / np.linalg.norm(xb))
+    out["solution_difference_mixed_vs_fp64_symmetric"] = float(np.linalg.norm(xa - xs) /
+                                                               np.linalg.norm(xs))
     out["workload"] = ("cube-64k: N=65536 uniform in the unit cube, 1/r, A_ii=2N^(1/3), "
                        "leaves<=64, Chebyshev 4^3, eps=1e-8, default rank cap n^D")
     return out

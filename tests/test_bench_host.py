@@ -45,3 +45,73 @@ def test_percentiles_and_rates():
     assert bench._pct([3.0, 1.0, 2.0], 50) == 2.0
     assert bench._pct(list(range(1, 101)), 99) == 99
     assert bench.whole_job_rate(10, 2, 2000.0) == pytest.approx(10.0)
+
+
+class _FakeTorch:
+    float64 = "f64"
+
+    @staticmethod
+    def empty(shape, dtype=None, device=None):
+        import numpy as np
+        return np.zeros(shape)
+
+
+class _FakeServer:
+    """Accepts requests while a system has fewer than 32 queued columns; a
+    worker takes up to 32 queued columns at a time, and a block completes on
+    a later poll -- the bounds the output ring relies on."""
+
+    class ServerError(Exception):
+        pass
+
+    def __init__(self):
+        self.queued, self.running, self.live, self.next = {}, {}, {}, 1
+
+    def ifmm_server_submit_device(self, srv, sid, b, x, N, tol, maxit):
+        q = self.queued.setdefault(sid, [])
+        if sum(k for k, _, _ in q) + b.shape[0] > 32:
+            raise self.ServerError()
+        t = self.next
+        self.next += 1
+        q.append((b.shape[0], t, x))
+        return t
+
+    def step(self):
+        for sid, q in self.queued.items():
+            if self.running.get(sid):
+                for _, t, _ in self.running[sid]:
+                    self.live.pop(t, None)
+                self.running[sid] = []
+            blk, cols = [], 0
+            while q and cols + q[0][0] <= 32:
+                k, t, x = q.pop(0)
+                blk.append((k, t, x))
+                cols += k
+            self.running[sid] = blk
+
+
+def test_output_ring_never_hands_live_columns_to_a_new_request():
+    """bench.Load's per-system output ring: every request's columns are free
+    of every request not yet completed (queued or running)."""
+    import numpy as np
+    srv = _FakeServer()
+    ifmm_ns = type("I", (), {"ServerError": _FakeServer.ServerError,
+                             "ifmm_server_submit_device": srv.ifmm_server_submit_device})
+    N = [5] * bench.N_SYSTEMS
+    pools = {i: np.zeros((32, 5)) for i in range(bench.N_SYSTEMS)}
+    load = bench.Load(ifmm_ns, None, [0] * bench.N_SYSTEMS, pools, np.random.default_rng(3), True,
+                      _FakeTorch, N)
+    for i in range(bench.N_SYSTEMS):
+        load.ring[i] = np.zeros((bench.RING_COLS, 5))
+    for step in range(4000):
+        load._submit(0.0)
+        if step % 7 == 0:
+            srv.step()
+        for i in range(bench.N_SYSTEMS):   # live = queued + running requests of system i
+            live = [x for _, _, x in srv.queued.get(i, [])] + \
+                   [x for _, _, x in srv.running.get(i, [])]
+            spans = sorted((x.__array_interface__["data"][0],
+                            x.__array_interface__["data"][0] + x.nbytes) for x in live)
+            for (a0, a1), (b0, b1) in zip(spans, spans[1:]):
+                assert a1 <= b0, "two outstanding requests share output columns"
+    assert load.shed > 0 and load.offered == 4000
