@@ -20,12 +20,17 @@ states.  Module map:
 * ``h2``         the raw H^2 operators (P2P, P2M/L2P, M2M/L2L, M2L), the FMM
                  matvec, dense assembly of the H^2 matrix A_n for small N, and
                  dense assembly of the extended sparse matrix E (Eq. Ax=b_extended).
+* ``h2_ortho``   the same A_n with orthonormal bases (Sec. 3: Chebyshev
+                 operators followed by an SVD) and sigma_0 of that extended
+                 matrix -- the alternative reading of sigma_0, unused by the
+                 default path.
 * ``ifmm``       sigma_0(E) by power iteration (Sec. 2.4), weighted initial
                  bases (footnote to Eq. U_j_recomp), level-by-level elimination
                  with fill-in compression and redirection (Algorithms 1-3),
                  merge to the parent (Eqs. y_merge-K_merge), top dense solve,
                  and the substitution phase.
-* ``gmres``      non-restarted right-preconditioned GMRES (Sec. 3.2).
+* ``gmres``      non-restarted GMRES with right or left preconditioning
+                 (Sec. 3.2, Appendix B) and block GMRES.
 
 Parity status of each function is stated in its module header.
 """

@@ -11,10 +11,12 @@
 //     into a double-buffered per-warp shared-memory stage while the previous
 //     entry is multiplied;
 //   * ndp = 8 RG with RG the smallest power of two with 8 RG >= nd (nd <= 64);
-//     lane (rg, cg) keeps the 8 rows rg*8 .. rg*8+7 of RG columns in registers
-//     (RG row groups, 32 / RG column groups), reading its 8 table values as
-//     16-byte broadcasts and its source values from a column stride of
-//     ndp + 16 / sizeof(T) elements (no bank conflicts);
+//     a pass of 32 columns gives lane (rg, cg) the 8 rows rg*8 .. rg*8+7 of RG
+//     columns in registers (RG row groups, 32 / RG column groups); passes of
+//     at most 8 columns or of one column use narrower tiles (UniTile), so a
+//     single right-hand side does not pay for 32; a lane reads its table
+//     values as 16-byte broadcasts and its source values from a column stride
+//     of ndp + 16 / sizeof(T) elements (no bank conflicts);
 //   * the sums over entries are taken in entry order, so results do not depend
 //     on scheduling.
 // Coefficient vectors are stored with ndp entries per box (16-byte aligned).

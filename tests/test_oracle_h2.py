@@ -65,3 +65,63 @@ def test_extended_apply_matches_dense():
     assert np.allclose(h.extended_apply(v, transpose=True), E.T @ v, atol=1e-10)
     # E is symmetric for a symmetric kernel (Sec. 2.1)
     assert np.allclose(E, E.T)
+
+
+# -- the orthonormal re-representation (oracle/h2_ortho.py; Sec. 3: Chebyshev
+# operators followed by an SVD, so the paper's E carries orthonormal bases) ----
+def _composed_basis(o, l, i):
+    """Orthonormal basis of box i at depth l over its points (tree order)."""
+    h2 = o.h2
+    if l == h2.L:
+        return o.Q[(l, i)]
+    ch = h2.tree.levels[l].children[i]
+    blocks = [_composed_basis(o, l + 1, c) for c in ch]
+    rows = sum(b.shape[0] for b in blocks)
+    cols = sum(b.shape[1] for b in blocks)
+    D = np.zeros((rows, cols))
+    r0 = c0 = 0
+    for b in blocks:
+        D[r0:r0 + b.shape[0], c0:c0 + b.shape[1]] = b
+        r0 += b.shape[0]
+        c0 += b.shape[1]
+    return D @ np.vstack([o.Tp[(l + 1, c)] for c in ch])
+
+
+@pytest.mark.parametrize("N,leaf,dim,n", [(400, 12, 3, 2), (500, 8, 2, 3), (700, 6, 3, 2)])
+def test_orthonormal_extended_system_solves_the_h2_system(N, leaf, dim, n):
+    """E' (orthonormal bases) eliminated onto x is the same A_n: solving
+    E' [x; z; y] = [b; 0; 0] gives the dense solve of A_n."""
+    from oracle.h2_ortho import OrthonormalH2
+    _, h = make(N, 3, n, leaf, dim)
+    o = OrthonormalH2(h)
+    E = o.extended_dense()
+    b = np.random.default_rng(4).standard_normal(N)
+    rhs = np.zeros(o.n)
+    rhs[:N] = b
+    x_ext = np.linalg.solve(E, rhs)[:N]
+    x = np.linalg.solve(h.dense_blockwise(), b)
+    assert np.linalg.norm(x_ext - x) / np.linalg.norm(x) < 1e-9
+    v = np.random.default_rng(6).standard_normal(o.n)
+    assert np.allclose(o.extended_apply(v), E @ v, atol=1e-10)
+    assert np.allclose(o.extended_apply(v, transpose=True), E.T @ v, atol=1e-10)
+
+
+def test_orthonormal_bases_are_orthonormal_at_every_depth():
+    from oracle.h2_ortho import OrthonormalH2
+    _, h = make(700, 6, 3, 2, 3)
+    assert h.L >= 3   # transfers are re-represented too
+    o = OrthonormalH2(h)
+    for l in range(2, h.L + 1):
+        for i in range(0, h.tree.levels[l].nb, 3):
+            B = _composed_basis(o, l, i)
+            assert np.allclose(B.T @ B, np.eye(B.shape[1]), atol=1e-12)
+            assert B.shape[1] <= min(B.shape[0], h.nd)
+
+
+def test_orthonormal_sigma0_is_the_largest_singular_value():
+    from oracle.h2_ortho import OrthonormalH2
+    _, h = make(500, 8, 2, 3)
+    o = OrthonormalH2(h)
+    s, it = o.sigma0_power(maxit=400, rtol=1e-9)
+    s_ref = np.linalg.svd(o.extended_dense(), compute_uv=False)[0]
+    assert abs(s - s_ref) <= 1e-4 * s_ref and it < 400
