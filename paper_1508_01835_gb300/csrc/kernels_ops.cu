@@ -153,15 +153,18 @@ __global__ void __launch_bounds__(256) k_direct(KSpec ks, int dim, const double*
 }
 
 // Block-row sparse product, one warp per job (SpJob), for FP64 and FP32.
-// A pass serves up to 32 right-hand sides from one read of the job's matrix
-// entries: the x values of 32 matrix columns at a time are staged in the
-// warp's shared memory ([k][column], row stride 32 + 16 / sizeof(T)); lane
-// (r, g) of a row tile of MR rows (MR = 8, 16 or 32 from the row's height)
-// keeps rows r of the MR columns g*MR .. g*MR+MR-1 in registers, reading its
-// A value once per k (transposed entries read along the stored row) and its
-// x values as 16-byte shared-memory loads.  Sums run over the job's segments
-// in order; split rows meet in k_spmm_reduce / k_spmm_f32_reduce in job order,
-// so results do not depend on scheduling.
+// A job is one tile of MR rows of a row (MR = 8, 16 or 32 from the row's
+// height; taller rows are several tiles) over a contiguous range of its
+// concatenated entry columns.  A pass serves up to NBT right-hand sides (4 or
+// 32) from one read of the job's matrix entries: for every chunk of KC entry
+// columns the warp copies the x values (NBT columns, [k][column] with row
+// stride NBT + 16 / sizeof(T)) and the tile's A values ([k][row]) into its
+// shared memory with cp.async, all of the chunk's copies in flight together;
+// lane (r, g) then keeps row r of the tile for the columns g*CPL ..
+// g*CPL+CPL-1 in registers (32 / MR column groups), reading one A value and
+// CPL x values (16-byte loads) per k.  Sums run over the job's segments in
+// order; a tile cut along k meets its partial sums in k_spmm_reduce /
+// k_spmm_f32_reduce in job order, so results do not depend on scheduling.
 constexpr int SW_WARPS = 8, SW_NB = 32;
 // k values per staged chunk: 32 (FP32) or 16 (FP64), so that a warp's stage
 // (x: KC x (NBT + pad), A: KC x MR) stays near 8 KB
