@@ -340,6 +340,26 @@ __global__ void __launch_bounds__(32 * SW_WARPS, 2)
   spmm_warp_job<T, MR, NBT>(R, ents, J, segs, part, pld, c0, nb, xs, lane);
 }
 
+// every row class in one launch: the warp's job picks its tile height (jobs
+// are grouped by class, so a CTA's warps mostly take the same branch)
+template <class T, int NBT>
+__global__ void __launch_bounds__(32 * SW_WARPS, 2)
+    k_spmm_warp_any(const typename SpT<T>::Row* __restrict__ rows,
+                    const typename SpT<T>::Ent* __restrict__ ents, const SpJob* __restrict__ jobs,
+                    int njobs, const SpSeg* __restrict__ segs, T* __restrict__ part,
+                    long long pld, int c0, int nb) {
+  extern __shared__ __align__(16) unsigned char sw_smem[];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int jb = blockIdx.x * SW_WARPS + w;
+  if (jb >= njobs) return;  // warp-uniform; no block-wide barrier in this kernel
+  T* xs = reinterpret_cast<T*>(sw_smem) + (size_t)w * sw_stage<T, 32, NBT>();
+  const SpJob J = jobs[jb];
+  const typename SpT<T>::Row R = rows[J.row];
+  if (R.m <= 8) spmm_warp_job<T, 8, NBT>(R, ents, J, segs, part, pld, c0, nb, xs, lane);
+  else if (R.m <= 16) spmm_warp_job<T, 16, NBT>(R, ents, J, segs, part, pld, c0, nb, xs, lane);
+  else spmm_warp_job<T, 32, NBT>(R, ents, J, segs, part, pld, c0, nb, xs, lane);
+}
+
 // row class of a job: 0 (m <= 8), 1 (m <= 16), 2 (m > 16)
 static int sw_class(int m) { return m <= 8 ? 0 : m <= 16 ? 1 : 2; }
 
@@ -361,11 +381,34 @@ static void launch_sw_class(const typename SpT<T>::Row* rows, const typename SpT
   else launch_sw_tile<T, MR, 32>(rows, ents, jobs, njobs, segs, part, pld, c0, nb, s);
 }
 
-// one launch per row class present (jobs grouped by class at plan time)
+template <class T, int NBT>
+static void launch_sw_any(const typename SpT<T>::Row* rows, const typename SpT<T>::Ent* ents,
+                          const SpJob* jobs, int njobs, const SpSeg* segs, T* part, long long pld,
+                          int c0, int nb, cudaStream_t s) {
+  const int smem = SW_WARPS * sw_stage<T, 32, NBT>() * (int)sizeof(T);
+  set_max_dynamic_smem((const void*)k_spmm_warp_any<T, NBT>, smem);
+  k_spmm_warp_any<T, NBT><<<(njobs + SW_WARPS - 1) / SW_WARPS, 32 * SW_WARPS, smem, s>>>(
+      rows, ents, jobs, njobs, segs, part, pld, c0, nb);
+}
+
+// Launch of a plan's jobs (grouped by row class at plan time): one kernel for
+// a single class, one kernel over all classes otherwise (IFMM_SPMM_SPLIT=1:
+// one launch per class)
 template <class T>
 static void launch_spmm_warp(const typename SpT<T>::Row* rows, const typename SpT<T>::Ent* ents,
                              const SpJob* jobs, const int* ncls, const SpSeg* segs, T* part,
                              long long pld, int c0, int nb, cudaStream_t s) {
+  static const bool split = [] {
+    const char* e = std::getenv("IFMM_SPMM_SPLIT");
+    return e && e[0] == '1';
+  }();
+  const int classes = (ncls[0] > 0) + (ncls[1] > 0) + (ncls[2] > 0);
+  if (classes > 1 && !split) {
+    const int njobs = ncls[0] + ncls[1] + ncls[2];
+    if (nb <= 4) launch_sw_any<T, 4>(rows, ents, jobs, njobs, segs, part, pld, c0, nb, s);
+    else launch_sw_any<T, 32>(rows, ents, jobs, njobs, segs, part, pld, c0, nb, s);
+    return;
+  }
   launch_sw_class<T, 8>(rows, ents, jobs, ncls[0], segs, part, pld, c0, nb, s);
   launch_sw_class<T, 16>(rows, ents, jobs + ncls[0], ncls[1], segs, part, pld, c0, nb, s);
   launch_sw_class<T, 32>(rows, ents, jobs + ncls[0] + ncls[1], ncls[2], segs, part, pld, c0, nb,
