@@ -8,8 +8,8 @@ fixed 5^3 Chebyshev FMM matvec.  Unpreconditioned and with the IFMM of order
 n = 1 the counts must be within 2 of the printed 78 and 19 (the point
 realisation differs); for every n the IFMM must cut the iteration count well
 below the unpreconditioned one and GMRES must reach the residual.  (For
-n >= 2 this build needs a few more iterations than printed; the reading of
-sigma_0(E) is the likely reason.)
+n >= 2 more iterations than printed are needed; the reading of sigma_0(E)
+alone does not explain the difference.)
 """
 import os
 
